@@ -1,0 +1,129 @@
+/*
+ * qams.h -- C ABI of the B300 multi-body Nystrom operator library (libqams).
+ *
+ * Problem (Sec. 2, Sec. 4): sound-soft scattering by several bodies, each a
+ * rigid motion x = R x0 + c (Sec. 6.5) of a quasi-axisymmetric reference
+ * shape (Eq. para_quasi, generalised to a planar-arc axis), solved with the
+ * combined-layer representation u = (D - i eta S)[mu] (Sec. 2, Remark) as the
+ * block system (Eq. linearsys)
+ *
+ *     (1/2 I + D - i eta S) mu = -u^inc .
+ *
+ * Conventions
+ *  - Every call returns int: QAMS_OK (0) or a negative QAMS_E* code;
+ *    qams_strerror() names it.  On error nothing has been launched unless
+ *    the code is QAMS_ECUDA.
+ *  - "_dev" pointers are caller-owned device buffers on the context's
+ *    device; "_host" pointers are caller-owned host buffers that are only
+ *    read (or written) during the call.
+ *  - Unknown vectors are [N][R] interleaved complex, node-major with the R
+ *    right-hand sides innermost: complex128 (double re, im) for
+ *    QAMS_PREC_FP64, complex64 (float re, im) for QAMS_PREC_FP32.
+ *    Node order: body -> panel -> Gauss-Legendre node -> azimuth (theta
+ *    fastest), the order of Eq. sx; qams_get_nodes() exposes it.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default).
+ *    Calls enqueue work on it and do not synchronise the device, except
+ *    where a call is documented as blocking.
+ *  - The library owns and frees (qams_destroy) its node tables, self
+ *    blocks, preconditioner and workspaces.  Host descriptors are copied.
+ */
+#ifndef QAMS_H
+#define QAMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  QAMS_OK = 0,
+  QAMS_EINVAL = -1,     /* bad argument or call order                     */
+  QAMS_EBUDGET = -2,    /* footprint above the context's HBM budget       */
+  QAMS_EGEOM = -3,      /* bodies overlap / closer than the minimum gap  */
+  QAMS_ENOCONV = -4,    /* iteration limit reached; stats still filled    */
+  QAMS_ENUMERIC = -5,   /* NaN/Inf in a residual                          */
+  QAMS_ETIMEOUT = -6,   /* a bounded device wait gave up                  */
+  QAMS_ECANCELLED = -7, /* cancelled between restart cycles               */
+  QAMS_ECUDA = -8       /* a CUDA runtime call failed                     */
+};
+
+enum { QAMS_PREC_FP64 = 0, QAMS_PREC_FP32 = 1 };
+
+typedef struct qams_ctx qams_ctx; /* opaque, library-owned */
+
+/* One body (all FP64, host memory, copied at qams_set_bodies).
+ * Reference shape, s in [-pi/2, pi/2], u = (1 + sin s)/2, l = L (u - 1/2):
+ *   rho(u) = base_radius (1 + sum_m mode_cos[m-1] cos 2 pi m u + mode_sin[m-1] sin 2 pi m u)
+ *   r(s)   = rho(u) cos s          (closed at both poles)
+ *   axis   = planar circular arc of curvature `curvature` and arclength L
+ *            with a rotation-minimising frame; 0 = straight (a body of
+ *            revolution);
+ *   y(s,theta) = gamma(l) + r(s) (cos theta e1(l) + sin theta e2).
+ * Discretisation (Sec. 3.1): n_panels uniform panels in s, `order`
+ * Gauss-Legendre nodes per panel, n_theta = 2N equispaced azimuths. */
+typedef struct {
+  int n_panels, order, n_theta;
+  double base_radius;
+  int n_modes; /* <= 8; mode_cos / mode_sin each hold n_modes values (NULL = zeros) */
+  const double* mode_cos;
+  const double* mode_sin;
+  double axis_length, curvature;
+  double rotation[9]; /* row-major R, world = R * local + center */
+  double center[3];
+} qams_body_desc;
+
+const char* qams_strerror(int code);
+
+/* Create a context on CUDA device `cuda_device`.  hbm_budget_bytes = 0 means
+ * no limit.  Errors: QAMS_EINVAL, QAMS_ECUDA. */
+int qams_create(qams_ctx** out, int cuda_device, size_t hbm_budget_bytes);
+void qams_destroy(qams_ctx* ctx);
+
+/* Bodies and their Nystrom nodes (Sec. 3.1, Eq. sx).  Builds positions,
+ * unit outward normals and weights w = |J| (pi/N) omega in FP64 on the host
+ * and uploads them.  Rejects (QAMS_EGEOM) bodies whose bounding balls come
+ * closer than min_gap (Sec. 4 separation assumption).  Blocking.
+ * Errors: QAMS_EINVAL (n_bodies < 1, n_theta odd or < 2, order < 1,
+ * n_panels < 1, n_modes > 8), QAMS_EGEOM, QAMS_EBUDGET, QAMS_ECUDA. */
+int qams_set_bodies(qams_ctx* ctx, int n_bodies, const qams_body_desc* bodies, double min_gap);
+
+/* N (total nodes) and the first node of every body (n_bodies+1 offsets). */
+int qams_node_count(const qams_ctx* ctx, long long* n_nodes);
+int qams_body_offsets(const qams_ctx* ctx, long long* offsets_host);
+
+/* Copy node tables to the host: x_host, n_host are [N][3], w_host is [N].
+ * Any pointer may be NULL.  Blocking. */
+int qams_get_nodes(const qams_ctx* ctx, double* x_host, double* n_host, double* w_host);
+
+/* Wavenumber k > 0 and combined-layer coupling eta (0 = pure double layer,
+ * Eq. multi-double; 1 = the default of the Sec. 2 Remark). */
+int qams_set_wavenumber(qams_ctx* ctx, double k, double eta);
+
+/* Inter-body smooth sum (Eq. multi2part, the off-diagonal blocks of Eq.
+ * linearsys applied matrix-free):
+ *   y_t = sum_{s on other bodies} K(x_t, y_s) sigma_s,
+ *   K   = e^{ik rho}/(4 pi rho) [(ik/rho - 1/rho^2) n_s.(y_s - x_t) - i eta],
+ * sigma = w mu with the quadrature weights already folded in.  sigma_dev and
+ * y_dev are [N][R] complex of the given precision; y is overwritten.
+ * QAMS_PREC_FP32 evaluates each pair in FP32 with the phase split per body
+ * pair, e^{ik rho} = e^{ik rho_0} e^{ik (rho - rho_0)}, rho_0 = |c_a - c_b|
+ * in FP64.  Errors: QAMS_EINVAL (R < 1, no bodies, no wavenumber). */
+int qams_pairsum(qams_ctx* ctx, int R, const void* sigma_dev, void* y_dev, int precision, void* stream);
+
+/* Right-hand sides b = -u^inc = -e^{ik d.x} (Sec. 6) for R unit directions
+ * dirs_host [R][3]; rhs_dev is [N][R] complex128. */
+int qams_incident_plane(qams_ctx* ctx, int R, const double* dirs_host, void* rhs_dev, void* stream);
+
+/* Far-field pattern of densities mu_dev [N][R] complex128 at M unit
+ * directions dirs_host [M][3] (Sec. 6, restated for the combined layer):
+ *   u_inf(xhat) = (1/4pi) sum_y (-ik xhat.n(y) - i eta) e^{-ik xhat.y} w mu.
+ * uinf_dev is [M][R] complex128. */
+int qams_farfield(qams_ctx* ctx, int R, const void* mu_dev, int M, const double* dirs_host,
+                  void* uinf_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QAMS_H */

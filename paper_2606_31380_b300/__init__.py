@@ -1,0 +1,11 @@
+"""B300-native multi-body Nystrom operator library (arXiv 2606.31380, Lai & Li).
+
+The compute path is the C-ABI shared library ``libqams.so`` (hand-written
+CUDA for sm_103a, declared in ``include/qams.h``).  This package is only its
+ctypes binding; there is no CPU fallback: importing it without the built
+library, or calling it without a CUDA device, raises.
+"""
+from ._binding import (PREC_FP32, PREC_FP64, Context, QamsError, body_desc_array, lib_path,  # noqa: F401
+                       load_library)
+
+__all__ = ["Context", "QamsError", "PREC_FP64", "PREC_FP32", "load_library", "lib_path", "body_desc_array"]

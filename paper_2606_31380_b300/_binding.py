@@ -1,0 +1,190 @@
+"""ctypes binding of libqams (argument marshalling only; all arithmetic runs in
+the library's CUDA kernels).  Tensors are torch CUDA tensors: complex128
+[N, R] for the FP64 path and complex64 [N, R] for the FP32 path."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+PREC_FP64 = 0
+PREC_FP32 = 1
+
+
+def lib_path() -> str:
+    return os.path.join(HERE, "libqams.so")
+
+
+class BodyDesc(C.Structure):
+    _fields_ = [("n_panels", C.c_int), ("order", C.c_int), ("n_theta", C.c_int),
+                ("base_radius", C.c_double), ("n_modes", C.c_int),
+                ("mode_cos", C.POINTER(C.c_double)), ("mode_sin", C.POINTER(C.c_double)),
+                ("axis_length", C.c_double), ("curvature", C.c_double),
+                ("rotation", C.c_double * 9), ("center", C.c_double * 3)]
+
+
+_LIB = None
+
+
+def load_library():
+    """Load the in-tree libqams.so; raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libqams.so is not built ({path}); run paper_2606_31380_b300/build.py")
+    lib = C.CDLL(path)
+    vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
+    sig = {
+        "qams_strerror": (C.c_char_p, [i]),
+        "qams_create": (i, [C.POINTER(vp), i, C.c_size_t]),
+        "qams_destroy": (None, [vp]),
+        "qams_set_bodies": (i, [vp, i, C.POINTER(BodyDesc), d]),
+        "qams_node_count": (i, [vp, C.POINTER(ll)]),
+        "qams_body_offsets": (i, [vp, C.POINTER(ll)]),
+        "qams_get_nodes": (i, [vp, vp, vp, vp]),
+        "qams_set_wavenumber": (i, [vp, d, d]),
+        "qams_pairsum": (i, [vp, i, vp, vp, i, vp]),
+        "qams_incident_plane": (i, [vp, i, vp, vp, vp]),
+        "qams_farfield": (i, [vp, i, vp, i, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class QamsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        lib = load_library()
+        super().__init__(f"{what}: {lib.qams_strerror(code).decode()} (code {code})")
+        self.code = code
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise QamsError(code, what)
+
+
+def body_desc_array(bodies) -> tuple:
+    """Marshal scene bodies (objects with the qams_body_desc fields) into a
+    ctypes array; returns (array, keep-alive list)."""
+    arr = (BodyDesc * len(bodies))()
+    keep = []
+    for dst, b in zip(arr, bodies):
+        nm = max(len(b.mode_cos), len(b.mode_sin))
+        a = np.zeros(nm)
+        s = np.zeros(nm)
+        a[: len(b.mode_cos)] = b.mode_cos
+        s[: len(b.mode_sin)] = b.mode_sin
+        ca = (C.c_double * max(nm, 1))(*a)
+        cs = (C.c_double * max(nm, 1))(*s)
+        keep += [ca, cs]
+        dst.n_panels, dst.order, dst.n_theta = b.n_panels, b.order, b.n_theta
+        dst.base_radius = b.base_radius
+        dst.n_modes = nm
+        dst.mode_cos = C.cast(ca, C.POINTER(C.c_double))
+        dst.mode_sin = C.cast(cs, C.POINTER(C.c_double))
+        dst.axis_length, dst.curvature = b.axis_length, b.curvature
+        dst.rotation = (C.c_double * 9)(*[float(v) for v in b.rotation])
+        dst.center = (C.c_double * 3)(*[float(v) for v in b.center])
+    return arr, keep
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _dev(t, dtype, shape, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{what}: expected contiguous {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One libqams context on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.lib = load_library()
+        self._h = C.c_void_p()
+        _check(self.lib.qams_create(C.byref(self._h), device, hbm_budget), "qams_create")
+        self.device = device
+        self.N = 0
+        self.R = 0
+
+    def close(self):
+        if self._h:
+            self.lib.qams_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- setup -------------------------------------------------------------
+    def set_bodies(self, bodies, min_gap: float = 0.0):
+        arr, keep = body_desc_array(bodies)
+        _check(self.lib.qams_set_bodies(self._h, len(bodies), arr, float(min_gap)), "qams_set_bodies")
+        n = C.c_longlong()
+        _check(self.lib.qams_node_count(self._h, C.byref(n)), "qams_node_count")
+        self.N = int(n.value)
+        self.n_bodies = len(bodies)
+
+    def body_offsets(self) -> np.ndarray:
+        off = np.zeros(self.n_bodies + 1, np.int64)
+        _check(self.lib.qams_body_offsets(self._h, off.ctypes.data_as(C.POINTER(C.c_longlong))),
+               "qams_body_offsets")
+        return off
+
+    def get_nodes(self):
+        x = np.zeros((self.N, 3))
+        n = np.zeros((self.N, 3))
+        w = np.zeros(self.N)
+        _check(self.lib.qams_get_nodes(self._h, x.ctypes.data_as(C.c_void_p), n.ctypes.data_as(C.c_void_p),
+                                       w.ctypes.data_as(C.c_void_p)), "qams_get_nodes")
+        return x, n, w
+
+    def set_wavenumber(self, k: float, eta: float = 1.0):
+        _check(self.lib.qams_set_wavenumber(self._h, float(k), float(eta)), "qams_set_wavenumber")
+        self.k, self.eta = float(k), float(eta)
+
+    # --- compute -----------------------------------------------------------
+    def pairsum(self, sigma, y, precision: int = PREC_FP64, stream=None):
+        import torch
+        R = sigma.shape[1]
+        dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
+        _check(self.lib.qams_pairsum(self._h, R, _dev(sigma, dt, (self.N, R), "sigma"),
+                                     _dev(y, dt, (self.N, R), "y"), precision, C.c_void_p(_stream_ptr(stream))),
+               "qams_pairsum")
+
+    def incident_plane(self, dirs: np.ndarray, rhs, stream=None):
+        import torch
+        dirs = np.ascontiguousarray(dirs, float)
+        R = dirs.shape[0]
+        _check(self.lib.qams_incident_plane(self._h, R, dirs.ctypes.data_as(C.c_void_p),
+                                            _dev(rhs, torch.complex128, (self.N, R), "rhs"),
+                                            C.c_void_p(_stream_ptr(stream))), "qams_incident_plane")
+
+    def farfield(self, mu, dirs: np.ndarray, uinf, stream=None):
+        import torch
+        dirs = np.ascontiguousarray(dirs, float)
+        M = dirs.shape[0]
+        R = mu.shape[1]
+        _check(self.lib.qams_farfield(self._h, R, _dev(mu, torch.complex128, (self.N, R), "mu"), M,
+                                      dirs.ctypes.data_as(C.c_void_p),
+                                      _dev(uinf, torch.complex128, (M, R), "uinf"),
+                                      C.c_void_p(_stream_ptr(stream))), "qams_farfield")

@@ -1,0 +1,193 @@
+// C ABI entry points (declared in include/qams.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "qams_internal.h"
+
+static thread_local char g_last_cuda[256];
+
+void qams_internal_last_cuda_error(cudaError_t e, const char* what) {
+  snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", what, cudaGetErrorString(e));
+}
+
+int qams_dev_alloc(qams_ctx* c, DeviceBuf* b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (c->budget && c->allocated + bytes > c->budget) return QAMS_EBUDGET;
+  QAMS_CUDA(cudaMalloc(&b->p, bytes));
+  b->bytes = bytes;
+  c->allocated += bytes;
+  return QAMS_OK;
+}
+
+void qams_dev_free(qams_ctx* c, DeviceBuf* b) {
+  if (b->p) {
+    cudaFree(b->p);
+    c->allocated -= b->bytes;
+  }
+  b->p = nullptr;
+  b->bytes = 0;
+}
+
+qams_ctx::~qams_ctx() {
+  cudaSetDevice(device);
+  for (DeviceBuf* b : {&x64, &n64, &x32, &n32, &centers, &boff, &d_tiles, &d_splits, &partial})
+    qams_dev_free(this, b);
+}
+
+extern "C" {
+
+const char* qams_strerror(int code) {
+  switch (code) {
+    case QAMS_OK: return "ok";
+    case QAMS_EINVAL: return "invalid argument or call order";
+    case QAMS_EBUDGET: return "footprint exceeds the context's HBM budget";
+    case QAMS_EGEOM: return "bodies overlap or violate the minimum gap";
+    case QAMS_ENOCONV: return "iteration limit reached";
+    case QAMS_ENUMERIC: return "non-finite residual";
+    case QAMS_ETIMEOUT: return "bounded device wait timed out";
+    case QAMS_ECANCELLED: return "cancelled";
+    case QAMS_ECUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
+    default: return "unknown error";
+  }
+}
+
+int qams_create(qams_ctx** out, int cuda_device, size_t hbm_budget_bytes) {
+  if (!out) return QAMS_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  QAMS_CUDA(cudaGetDeviceCount(&count));
+  if (cuda_device < 0 || cuda_device >= count) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(cuda_device));
+  qams_ctx* c = new qams_ctx();
+  c->device = cuda_device;
+  c->budget = hbm_budget_bytes;
+  *out = c;
+  return QAMS_OK;
+}
+
+void qams_destroy(qams_ctx* ctx) { delete ctx; }
+
+int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, double min_gap) {
+  if (!c || n_bodies < 1 || !bodies) return QAMS_EINVAL;
+  std::vector<BodyHost> bh(n_bodies);
+  std::vector<double> rad(n_bodies);
+  for (int i = 0; i < n_bodies; ++i) {
+    const qams_body_desc& d = bodies[i];
+    if (d.n_panels < 1 || d.order < 1 || d.n_theta < 2 || (d.n_theta & 1) || d.n_modes < 0 ||
+        d.n_modes > 8 || !(d.base_radius > 0) || !(d.axis_length > 0) || d.curvature < 0)
+      return QAMS_EINVAL;
+    bh[i].d = d;
+    bh[i].a.assign(d.n_modes, 0.0);
+    bh[i].b.assign(d.n_modes, 0.0);
+    double amp = 0.0;
+    for (int m = 0; m < d.n_modes; ++m) {
+      if (d.mode_cos) bh[i].a[m] = d.mode_cos[m];
+      if (d.mode_sin) bh[i].b[m] = d.mode_sin[m];
+      amp += std::fabs(bh[i].a[m]) + std::fabs(bh[i].b[m]);
+    }
+    if (amp >= 1.0 || d.curvature * d.base_radius * (1.0 + amp) >= 1.0) return QAMS_EINVAL;
+    bh[i].d.mode_cos = bh[i].a.data();
+    bh[i].d.mode_sin = bh[i].b.data();
+    rad[i] = 0.5 * d.axis_length + d.base_radius * (1.0 + amp);
+  }
+  for (int i = 0; i < n_bodies; ++i)
+    for (int j = i + 1; j < n_bodies; ++j) {
+      double dx = bodies[i].center[0] - bodies[j].center[0];
+      double dy = bodies[i].center[1] - bodies[j].center[1];
+      double dz = bodies[i].center[2] - bodies[j].center[2];
+      if (std::sqrt(dx * dx + dy * dy + dz * dz) < rad[i] + rad[j] + min_gap) return QAMS_EGEOM;
+    }
+  QAMS_CUDA(cudaSetDevice(c->device));
+  for (DeviceBuf* b : {&c->x64, &c->n64, &c->x32, &c->n32, &c->centers, &c->boff}) qams_dev_free(c, b);
+  c->bodies = std::move(bh);
+  int rc = qams_build_nodes(c);
+  if (rc) return rc;
+  const long long N = c->N;
+  const int nb = n_bodies;
+  std::vector<double> x4(4 * N), n4(4 * N), cen(4 * nb);
+  std::vector<float> xl(4 * N), nl(4 * N);
+  std::vector<long long> off(nb + 1);
+  for (int b = 0; b < nb; ++b) {
+    const BodyHost& B = c->bodies[b];
+    off[b] = B.offset;
+    for (int r = 0; r < 3; ++r) cen[4 * b + r] = B.d.center[r];
+    cen[4 * b + 3] = 0.0;
+    for (long long t = B.offset; t < B.offset + B.n; ++t) {
+      for (int r = 0; r < 3; ++r) {
+        x4[4 * t + r] = c->hx[3 * t + r];
+        n4[4 * t + r] = c->hn[3 * t + r];
+        xl[4 * t + r] = (float)(c->hx[3 * t + r] - B.d.center[r]);
+        nl[4 * t + r] = (float)c->hn[3 * t + r];
+      }
+      x4[4 * t + 3] = c->hw[t];
+      n4[4 * t + 3] = 0.0;
+      xl[4 * t + 3] = (float)c->hw[t];
+      nl[4 * t + 3] = 0.0f;
+    }
+  }
+  off[nb] = N;
+  if ((rc = qams_dev_alloc(c, &c->x64, sizeof(double) * 4 * N))) return rc;
+  if ((rc = qams_dev_alloc(c, &c->n64, sizeof(double) * 4 * N))) return rc;
+  if ((rc = qams_dev_alloc(c, &c->x32, sizeof(float) * 4 * N))) return rc;
+  if ((rc = qams_dev_alloc(c, &c->n32, sizeof(float) * 4 * N))) return rc;
+  if ((rc = qams_dev_alloc(c, &c->centers, sizeof(double) * 4 * nb))) return rc;
+  if ((rc = qams_dev_alloc(c, &c->boff, sizeof(long long) * (nb + 1)))) return rc;
+  QAMS_CUDA(cudaMemcpy(c->x64.p, x4.data(), sizeof(double) * 4 * N, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->n64.p, n4.data(), sizeof(double) * 4 * N, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->x32.p, xl.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->n32.p, nl.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->centers.p, cen.data(), sizeof(double) * 4 * nb, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->boff.p, off.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice));
+  return qams_pairsum_prepare(c);
+}
+
+int qams_node_count(const qams_ctx* c, long long* n) {
+  if (!c || !n) return QAMS_EINVAL;
+  *n = c->N;
+  return QAMS_OK;
+}
+
+int qams_body_offsets(const qams_ctx* c, long long* off) {
+  if (!c || !off || c->bodies.empty()) return QAMS_EINVAL;
+  for (size_t b = 0; b < c->bodies.size(); ++b) off[b] = c->bodies[b].offset;
+  off[c->bodies.size()] = c->N;
+  return QAMS_OK;
+}
+
+int qams_get_nodes(const qams_ctx* c, double* x, double* n, double* w) {
+  if (!c || c->bodies.empty()) return QAMS_EINVAL;
+  if (x) std::memcpy(x, c->hx.data(), sizeof(double) * 3 * c->N);
+  if (n) std::memcpy(n, c->hn.data(), sizeof(double) * 3 * c->N);
+  if (w) std::memcpy(w, c->hw.data(), sizeof(double) * c->N);
+  return QAMS_OK;
+}
+
+int qams_set_wavenumber(qams_ctx* c, double k, double eta) {
+  if (!c || !(k > 0) || !std::isfinite(k) || !std::isfinite(eta)) return QAMS_EINVAL;
+  c->k = k;
+  c->eta = eta;
+  c->have_k = true;
+  return QAMS_OK;
+}
+
+int qams_pairsum(qams_ctx* c, int R, const void* sigma, void* y, int precision, void* stream) {
+  if (!c || R < 1 || !sigma || !y || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
+  if (precision != QAMS_PREC_FP64 && precision != QAMS_PREC_FP32) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  return qams_pairsum_launch(c, R, sigma, y, precision, (cudaStream_t)stream);
+}
+
+int qams_incident_plane(qams_ctx* c, int R, const double* dirs, void* rhs, void* stream) {
+  if (!c || R < 1 || !dirs || !rhs || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  return qams_incident_launch(c, R, dirs, rhs, (cudaStream_t)stream);
+}
+
+int qams_farfield(qams_ctx* c, int R, const void* mu, int M, const double* dirs, void* uinf, void* stream) {
+  if (!c || R < 1 || M < 1 || !mu || !dirs || !uinf || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  return qams_farfield_launch(c, R, mu, M, dirs, uinf, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,330 @@
+// Inter-body pair sum (Eq. multi2part): the off-diagonal blocks of Eq.
+// linearsys applied matrix-free,
+//   y_t = sum_{s not in body(t)} K(x_t, y_s) sigma_s,
+//   K   = e^{ik rho}/(4 pi rho) [(ik/rho - 1/rho^2) n_s.(y_s - x_t) - i eta].
+//
+// Work decomposition: a CTA owns TILE consecutive targets of one body (one
+// per thread) and a contiguous range of source bodies; sources are staged
+// CHUNK at a time in shared memory and read as broadcasts.  With several
+// source ranges per tile the partial sums go to a [split][N][rc] buffer and
+// a second kernel adds them in a fixed order (deterministic result).
+//
+// FP32 path: positions are body-local, x = c_b + x~.  For a body pair (a,b)
+// with dc = c_a - c_b (FP64), rho0 = |dc| and d = x~_t - y~_s:
+//   rho^2 = rho0^2 + e,  e = 2 dc.d + |d|^2,  rho - rho0 = e/(rho + rho0),
+// so the phase k(rho - rho0) is formed from O(|d|) quantities and the large
+// part e^{ik rho0} is applied once per (target, source body) in FP64.
+#include <cmath>
+
+#include "qams_internal.h"
+
+namespace {
+
+constexpr int TILE = 128;
+constexpr int CHUNK = 128;
+constexpr float INV_2PI = 0.15915494309189535f;
+constexpr float TWO_PI_HI = 6.28318548202514648f;    // float(2 pi)
+constexpr float TWO_PI_LO = -1.7484555314695172e-7f;  // 2 pi - TWO_PI_HI
+
+template <int RC>
+__global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
+    const TargetTile* __restrict__ tiles, const SourceSplit* __restrict__ splits,
+    const long long* __restrict__ boff, const qd4* __restrict__ centers,
+    const float4* __restrict__ x32, const float4* __restrict__ n32, const float2* __restrict__ sigma,
+    int R, int r0, double k, double eta, float2* __restrict__ out, long long split_stride, int out_ld,
+    int out_r0) {
+  __shared__ float4 sp[CHUNK];
+  __shared__ float4 sq[CHUNK];
+  __shared__ float2 ss[CHUNK][RC];
+
+  const TargetTile tile = tiles[blockIdx.x];
+  const SourceSplit split = splits[blockIdx.y];
+  const int tid = threadIdx.x;
+  const bool active = tid < tile.count;
+  const long long t = tile.start + (active ? tid : 0);
+  const float4 xt = x32[t];
+  const qd4 ca = centers[tile.body];
+  const float kf = (float)k, etaf = (float)eta;
+
+  float2 tot[RC];
+#pragma unroll
+  for (int r = 0; r < RC; ++r) tot[r] = make_float2(0.f, 0.f);
+
+  for (int b = split.begin; b < split.end; ++b) {
+    if (b == tile.body) continue;
+    const qd4 cb = centers[b];
+    const double dcx = ca.x - cb.x, dcy = ca.y - cb.y, dcz = ca.z - cb.z;
+    const double rho0 = sqrt(dcx * dcx + dcy * dcy + dcz * dcz);
+    double s0d, c0d;
+    sincos(k * rho0, &s0d, &c0d);
+    const float fx = (float)dcx, fy = (float)dcy, fz = (float)dcz;
+    const float rho0f = (float)rho0;
+    const float r02 = (float)(rho0 * rho0);
+    const float At = fx * xt.x + fy * xt.y + fz * xt.z;
+
+    float2 acc[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) acc[r] = make_float2(0.f, 0.f);
+
+    const long long send = boff[b + 1];
+    for (long long s0 = boff[b]; s0 < send; s0 += CHUNK) {
+      __syncthreads();
+      const long long i = s0 + tid;
+      if (i < send) {
+        float4 p = x32[i];
+        float4 q = n32[i];
+        p.w = fx * p.x + fy * p.y + fz * p.z;  // dc . y~_s
+        q.w = fx * q.x + fy * q.y + fz * q.z;  // n_s . dc
+        sp[tid] = p;
+        sq[tid] = q;
+#pragma unroll
+        for (int r = 0; r < RC; ++r) ss[tid][r] = sigma[i * R + r0 + r];
+      }
+      __syncthreads();
+      const int cnt = (int)min((long long)CHUNK, send - s0);
+#pragma unroll 4
+      for (int j = 0; j < cnt; ++j) {
+        const float4 p = sp[j];
+        const float4 q = sq[j];
+        const float dx = xt.x - p.x, dy = xt.y - p.y, dz = xt.z - p.z;
+        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float e = fmaf(2.f, At - p.w, dd);
+        const float r2 = r02 + e;
+        const float rinv = rsqrtf(r2);
+        const float rho = r2 * rinv;
+        const float delta = __fdividef(e, rho + rho0f);
+        const float ph = kf * delta;
+        const float nq = rintf(ph * INV_2PI);
+        float red = fmaf(-nq, TWO_PI_HI, ph);
+        red = fmaf(-nq, TWO_PI_LO, red);
+        float sn, cs;
+        __sincosf(red, &sn, &cs);
+        const float nyx = -(q.w + fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz)));
+        const float are = -nyx * rinv * rinv;
+        const float aim = fmaf(kf * nyx, rinv, -etaf);
+        const float kre = (cs * are - sn * aim) * rinv;
+        const float kim = (sn * are + cs * aim) * rinv;
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+          const float2 s = ss[j][r];
+          acc[r].x = fmaf(kre, s.x, fmaf(-kim, s.y, acc[r].x));
+          acc[r].y = fmaf(kre, s.y, fmaf(kim, s.x, acc[r].y));
+        }
+      }
+    }
+    const float c0 = (float)c0d, s0f = (float)s0d;
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+      tot[r].x += c0 * acc[r].x - s0f * acc[r].y;
+      tot[r].y += c0 * acc[r].y + s0f * acc[r].x;
+    }
+  }
+  if (active) {
+    const float inv4pi = 0.079577471545947668f;
+    float2* o = out + split_stride * blockIdx.y + t * out_ld + out_r0;
+#pragma unroll
+    for (int r = 0; r < RC; ++r) o[r] = make_float2(tot[r].x * inv4pi, tot[r].y * inv4pi);
+  }
+}
+
+template <int RC>
+__global__ void __launch_bounds__(TILE) pairsum_f64_kernel(
+    const TargetTile* __restrict__ tiles, const SourceSplit* __restrict__ splits,
+    const long long* __restrict__ boff, const qd4* __restrict__ x64, const qd4* __restrict__ n64,
+    const double2* __restrict__ sigma, int R, int r0, double k, double eta, double2* __restrict__ out,
+    long long split_stride, int out_ld, int out_r0) {
+  __shared__ qd4 sp[CHUNK];
+  __shared__ qd4 sq[CHUNK];
+  __shared__ double2 ss[CHUNK][RC];
+
+  const TargetTile tile = tiles[blockIdx.x];
+  const SourceSplit split = splits[blockIdx.y];
+  const int tid = threadIdx.x;
+  const bool active = tid < tile.count;
+  const long long t = tile.start + (active ? tid : 0);
+  const qd4 xt = x64[t];
+
+  double2 acc[RC];
+#pragma unroll
+  for (int r = 0; r < RC; ++r) acc[r] = make_double2(0.0, 0.0);
+
+  for (int b = split.begin; b < split.end; ++b) {
+    if (b == tile.body) continue;
+    const long long send = boff[b + 1];
+    for (long long s0 = boff[b]; s0 < send; s0 += CHUNK) {
+      __syncthreads();
+      const long long i = s0 + tid;
+      if (i < send) {
+        sp[tid] = x64[i];
+        sq[tid] = n64[i];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) ss[tid][r] = sigma[i * R + r0 + r];
+      }
+      __syncthreads();
+      const int cnt = (int)min((long long)CHUNK, send - s0);
+#pragma unroll 2
+      for (int j = 0; j < cnt; ++j) {
+        const qd4 p = sp[j];
+        const qd4 q = sq[j];
+        const double dx = p.x - xt.x, dy = p.y - xt.y, dz = p.z - xt.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double rinv = rsqrt(r2);
+        const double rho = r2 * rinv;
+        double sn, cs;
+        sincos(k * rho, &sn, &cs);
+        const double nyx = q.x * dx + q.y * dy + q.z * dz;
+        const double are = -nyx * rinv * rinv;
+        const double aim = k * nyx * rinv - eta;
+        const double kre = (cs * are - sn * aim) * rinv;
+        const double kim = (sn * are + cs * aim) * rinv;
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+          const double2 s = ss[j][r];
+          acc[r].x += kre * s.x - kim * s.y;
+          acc[r].y += kre * s.y + kim * s.x;
+        }
+      }
+    }
+  }
+  if (active) {
+    const double inv4pi = 0.079577471545947667884;
+    double2* o = out + split_stride * blockIdx.y + t * out_ld + out_r0;
+#pragma unroll
+    for (int r = 0; r < RC; ++r) o[r] = make_double2(acc[r].x * inv4pi, acc[r].y * inv4pi);
+  }
+}
+
+// y[t][r0 + r] = sum over splits of part[split][t][r], r < rc (fixed order)
+template <typename C>
+__global__ void reduce_splits_kernel(const C* __restrict__ part, int S, long long N, int rc, C* __restrict__ y,
+                                     int R, int r0) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= N * rc) return;
+  const long long t = idx / rc;
+  const int r = (int)(idx % rc);
+  C s = part[idx];
+  for (int q = 1; q < S; ++q) {
+    const C v = part[q * N * rc + idx];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  y[t * R + r0 + r] = s;
+}
+
+int pick_rc(int left) {
+  if (left >= 16) return 16;
+  if (left >= 8) return 8;
+  if (left >= 4) return 4;
+  if (left >= 2) return 2;
+  return 1;
+}
+
+template <int RC>
+void launch_f32(qams_ctx* c, dim3 grid, const float2* sigma, int R, int r0, float2* out, long long stride,
+                int ld, int or0, cudaStream_t st) {
+  pairsum_f32_kernel<RC><<<grid, TILE, 0, st>>>(
+      (const TargetTile*)c->d_tiles.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
+      (const qd4*)c->centers.p, (const float4*)c->x32.p, (const float4*)c->n32.p, sigma, R, r0, c->k,
+      c->eta, out, stride, ld, or0);
+}
+
+template <int RC>
+void launch_f64(qams_ctx* c, dim3 grid, const double2* sigma, int R, int r0, double2* out, long long stride,
+                int ld, int or0, cudaStream_t st) {
+  pairsum_f64_kernel<RC><<<grid, TILE, 0, st>>>(
+      (const TargetTile*)c->d_tiles.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
+      (const qd4*)c->x64.p, (const qd4*)c->n64.p, sigma, R, r0, c->k, c->eta, out, stride, ld, or0);
+}
+
+}  // namespace
+
+// Build target tiles and source splits for the current bodies.
+int qams_pairsum_prepare(qams_ctx* c) {
+  c->tiles.clear();
+  for (int b = 0; b < (int)c->bodies.size(); ++b) {
+    const BodyHost& bh = c->bodies[b];
+    for (int s = 0; s < bh.n; s += TILE) c->tiles.push_back({b, std::min(TILE, bh.n - s), bh.offset + s});
+  }
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const long long want = 8LL * sms;  // CTAs for a couple of waves
+  const int nb = (int)c->bodies.size();
+  int S = (int)std::max(1LL, std::min<long long>(nb, (want + (long long)c->tiles.size() - 1) /
+                                                         (long long)c->tiles.size()));
+  c->splits.clear();
+  // contiguous body ranges with about N/S nodes each
+  long long per = (c->N + S - 1) / S, acc = 0;
+  int begin = 0;
+  for (int b = 0; b < nb; ++b) {
+    acc += c->bodies[b].n;
+    if (acc >= per * ((long long)c->splits.size() + 1) || b == nb - 1) {
+      c->splits.push_back({begin, b + 1});
+      begin = b + 1;
+    }
+  }
+  qams_dev_free(c, &c->d_tiles);
+  qams_dev_free(c, &c->d_splits);
+  qams_dev_free(c, &c->partial);
+  int rc = qams_dev_alloc(c, &c->d_tiles, sizeof(TargetTile) * c->tiles.size());
+  if (rc) return rc;
+  rc = qams_dev_alloc(c, &c->d_splits, sizeof(SourceSplit) * c->splits.size());
+  if (rc) return rc;
+  QAMS_CUDA(cudaMemcpy(c->d_tiles.p, c->tiles.data(), sizeof(TargetTile) * c->tiles.size(),
+                       cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->d_splits.p, c->splits.data(), sizeof(SourceSplit) * c->splits.size(),
+                       cudaMemcpyHostToDevice));
+  if (c->splits.size() > 1) {
+    rc = qams_dev_alloc(c, &c->partial, sizeof(double2) * 16 * (size_t)c->N * c->splits.size());
+    if (rc) return rc;
+  }
+  return QAMS_OK;
+}
+
+int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int precision, cudaStream_t st) {
+  const int S = (int)c->splits.size();
+  dim3 grid((unsigned)c->tiles.size(), (unsigned)S);
+  for (int r0 = 0; r0 < R;) {
+    const int rc = pick_rc(R - r0);
+    if (precision == QAMS_PREC_FP32) {
+      float2* out = S > 1 ? (float2*)c->partial.p : (float2*)y;
+      const long long stride = S > 1 ? c->N * rc : 0;
+      const int ld = S > 1 ? rc : R, or0 = S > 1 ? 0 : r0;
+      const float2* sg = (const float2*)sigma;
+      switch (rc) {
+        case 16: launch_f32<16>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        case 8: launch_f32<8>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        case 4: launch_f32<4>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        case 2: launch_f32<2>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        default: launch_f32<1>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+      }
+      QAMS_CUDA(cudaGetLastError());
+      if (S > 1) {
+        const long long n = c->N * rc;
+        reduce_splits_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            (const float2*)c->partial.p, S, c->N, rc, (float2*)y, R, r0);
+        QAMS_CUDA(cudaGetLastError());
+      }
+    } else {
+      double2* out = S > 1 ? (double2*)c->partial.p : (double2*)y;
+      const long long stride = S > 1 ? c->N * rc : 0;
+      const int ld = S > 1 ? rc : R, or0 = S > 1 ? 0 : r0;
+      const double2* sg = (const double2*)sigma;
+      switch (rc) {
+        case 16: launch_f64<16>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        case 8: launch_f64<8>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        case 4: launch_f64<4>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        case 2: launch_f64<2>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        default: launch_f64<1>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+      }
+      QAMS_CUDA(cudaGetLastError());
+      if (S > 1) {
+        const long long n = c->N * rc;
+        reduce_splits_kernel<double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            (const double2*)c->partial.p, S, c->N, rc, (double2*)y, R, r0);
+        QAMS_CUDA(cudaGetLastError());
+      }
+    }
+    r0 += rc;
+  }
+  return QAMS_OK;
+}

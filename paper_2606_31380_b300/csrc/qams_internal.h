@@ -1,0 +1,92 @@
+// Internal state of a libqams context (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qams.h"
+
+// 32-byte aligned double4 (one 256-bit load); cudaMalloc and the shared
+// arrays below satisfy the alignment.
+typedef double4_32a qd4;
+
+#define QAMS_CUDA(call)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) {                             \
+      qams_internal_last_cuda_error(e_, #call);          \
+      return QAMS_ECUDA;                                 \
+    }                                                    \
+  } while (0)
+
+void qams_internal_last_cuda_error(cudaError_t e, const char* what);
+
+struct BodyHost {
+  qams_body_desc d;          // pointers below are re-pointed at the copies
+  std::vector<double> a, b;  // profile Fourier modes
+  long long offset = 0;      // first node
+  int n = 0;                 // nodes
+};
+
+// One target tile of the pair sum: up to TILE consecutive nodes of one body.
+struct TargetTile {
+  int body;
+  int count;
+  long long start;
+};
+
+// A contiguous range of source bodies handled by one grid row.
+struct SourceSplit {
+  int begin, end;
+};
+
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct qams_ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t allocated = 0;
+  std::vector<BodyHost> bodies;
+  long long N = 0;
+  double k = 0.0, eta = 1.0;
+  bool have_k = false;
+
+  // host node tables (FP64, world frame)
+  std::vector<double> hx, hn, hw;  // [N][3], [N][3], [N]
+
+  // device node tables
+  DeviceBuf x64;     // double4 [N]: world position, w in .w
+  DeviceBuf n64;     // double4 [N]: world normal
+  DeviceBuf x32;     // float4  [N]: body-local position x - c_b, w in .w
+  DeviceBuf n32;     // float4  [N]: world normal
+  DeviceBuf centers; // double4 [nb]
+  DeviceBuf boff;    // long long [nb+1]
+
+  // pair-sum launch tables
+  std::vector<TargetTile> tiles;
+  std::vector<SourceSplit> splits;
+  DeviceBuf d_tiles, d_splits;
+  DeviceBuf partial;  // [splits][N][rc] partial sums (complex, largest precision)
+
+  ~qams_ctx();
+};
+
+int qams_dev_alloc(qams_ctx* c, DeviceBuf* b, size_t bytes);
+void qams_dev_free(qams_ctx* c, DeviceBuf* b);
+
+// geometry.cpp
+int qams_build_nodes(qams_ctx* c);
+void qams_gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+
+// pairsum.cu
+int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int precision, cudaStream_t st);
+int qams_pairsum_prepare(qams_ctx* c);
+
+// fields.cu
+int qams_incident_launch(qams_ctx* c, int R, const double* dirs_host, void* rhs, cudaStream_t st);
+int qams_farfield_launch(qams_ctx* c, int R, const void* mu, int M, const double* dirs_host, void* uinf,
+                         cudaStream_t st);

@@ -1,0 +1,39 @@
+"""The C-ABI library loads and exports every entry point include/qams.h declares
+(no compute call: runs without a GPU)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "qams.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qams_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_entry_points():
+    names = declared()
+    for must in ["qams_create", "qams_destroy", "qams_set_bodies", "qams_pairsum", "qams_farfield"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2606_31380_b300 as q
+    lib = q.load_library()
+    for name in declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", q.lib_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(qams_\w+)", out))
+    assert set(declared()) <= exported
+
+
+def test_errors_without_device_are_reported_not_crashing():
+    import ctypes as C
+    import paper_2606_31380_b300 as q
+    lib = q.load_library()
+    assert lib.qams_strerror(-3).decode().startswith("bodies overlap")
+    assert lib.qams_create(None, 0, 0) == -1  # out == NULL -> QAMS_EINVAL

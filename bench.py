@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the multi-body Nystrom solve on B300.
+
+One step = one full mixed-precision solve of a seeded scene: self-block
+assembly for the wavenumber, incident right-hand sides, GMRES with the FP32
+operator inside FP64 iterative refinement to ||b - A mu|| <= 1e-11 ||b||, and
+the far field on 200 x 200 directions.  Geometry (qams_set_bodies) is
+resident before the timed region; the e2e figure repeats the step through
+the C ABI starting from host descriptors and ending with the densities and
+far field copied back to host memory.
+
+value = Nystrom pair-interactions per second over the whole step: the
+pair-sum evaluations of every operator apply in the solve (N^2 - sum n_b^2
+per apply and right-hand side) divided by the step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Nyström pair-interactions/s, solves/s at 1e-8 rel err; p50/p99 solve latency"
+UNIT = "pair-interactions/s"
+FAR_DIRS = 200  # 200 x 200 far-field directions (Sec. 6)
+
+
+def far_directions(n=FAR_DIRS):
+    import numpy as np
+    th = (np.arange(n) + 0.5) * math.pi / n
+    ph = np.arange(n) * 2 * math.pi / n
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    return np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def fp64_peak_tflops(torch):
+    """Dense FP64 rate measured on this GPU (cuBLAS DGEMM 8192^3, best of 5)."""
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def assembly_flops(scene):
+    """Algorithmic FP64 operations of one self-block assembly, counted from the
+    kernel's dense loops per outer quadrature node (cosine transforms,
+    convolutions, Lagrange weights, accumulation); transcendental calls and
+    the Q recursions are not counted, so this undercounts the work."""
+    import numpy as np
+    total = 0.0
+    for b in scene.bodies:
+        order, nth, npan = b.order, b.n_theta, b.n_panels
+        N = nth // 2
+        amp = sum(abs(x) for x in b.mode_cos) + sum(abs(x) for x in b.mode_sin)
+        n1 = math.ceil(1.3 * scene.k * b.base_radius * (1 + amp) + 16.0)
+        M2 = n1 + 8
+        per_node = (2 * 3 * (n1 + 2) * (M2 - 1) + 15 * (N + 1) * (2 * n1 + 1) + 21 * nth * N + 11 * order * nth)
+        x, _ = np.polynomial.legendre.leggauss(order)
+        pw = math.pi / npan
+        nodes_per_row = 0
+        for p in range(npan):
+            for l in range(order):
+                s_t = -math.pi / 2 + pw * (p + 0.5 + 0.5 * x[l])
+                dpole = min(s_t + math.pi / 2, math.pi / 2 - s_t)
+                cnt = 0
+                for i in range(max(0, p - 1), min(npan - 1, p + 1) + 1):
+                    lo, hi = -math.pi / 2 + pw * i, -math.pi / 2 + pw * (i + 1)
+                    if i == p:
+                        for L in (abs(lo - s_t), abs(hi - s_t)):
+                            K = min(14, max(5, math.ceil(math.log2(L / (0.5 * dpole)))))
+                            cnt += K * (order + 4) + 20
+                    else:
+                        cnt += 6 * (order + 4) + 16
+                nodes_per_row += cnt * nth
+        total += nodes_per_row * per_node
+    return total
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2606_31380_b300 as q
+    import scenes
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    sc = scenes.config(args.config, request_id=rank)  # replicas: independent request per rank
+    R = sc.n_rhs
+    xh = far_directions()
+    M = xh.shape[0]
+    ctx = q.Context(local_rank)
+    ctx.set_bodies(sc.bodies)
+    ctx.set_wavenumber(sc.k, sc.eta)
+    N = ctx.N
+    pairs = sc.pair_count()
+    b = torch.zeros((N, R), dtype=torch.complex128, device="cuda")
+    mu = torch.zeros_like(b)
+    u = torch.zeros((M, R), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(record=None):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        ctx.assemble()
+        ev[1].record()
+        ctx.incident_plane(sc.directions, b)
+        st = ctx.solve(b, mu, q.PREC_FP32, tol=1e-11)
+        ev[2].record()
+        ctx.farfield(mu, xh, u)
+        ev[3].record()
+        if record is not None:
+            record.append((ev, st))
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = q.kernel_launches()
+    recs = []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(args.steps):
+        step(recs)
+    t1.record()
+    torch.cuda.synchronize()
+    launches = q.kernel_launches() - launches0
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    if dist:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+        dist.barrier()
+    step_ms = [r[0][0].elapsed_time(r[0][3]) for r in recs]
+    asm_ms = [r[0][0].elapsed_time(r[0][1]) for r in recs]
+    solve_ms = [r[0][1].elapsed_time(r[0][2]) for r in recs]
+    ff_ms = [r[0][2].elapsed_time(r[0][3]) for r in recs]
+    applies = [r[1]["applies_fp32"] + r[1]["applies_fp64"] for r in recs]
+    pair_evals = sum(a * pairs * R for a in applies)
+    value = pair_evals * world / elapsed  # every rank solves its own request of the same size
+
+    # accuracy of the mixed result against the plain FP64 GPU solve of the same scene
+    mu64 = torch.zeros_like(b)
+    ctx.solve(b, mu64, q.PREC_FP64, tol=1e-12)
+    rel_err = float(torch.linalg.norm(mu - mu64) / torch.linalg.norm(mu64))
+
+    # dominant kernel: self-block assembly (FP64 ALU) -- time it alone with events
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.assemble()
+    e1.record()
+    torch.cuda.synchronize()
+    asm_alone = e0.elapsed_time(e1) / 1e3
+    flops = assembly_flops(sc)
+    peak64 = 1.25
+    peak64_meas = fp64_peak_tflops(torch)
+
+    # FP32 apply pair rate (hot loop of the inner solver)
+    x32 = torch.randn((N, R), dtype=torch.complex64, device="cuda")
+    y32 = torch.empty_like(x32)
+    ctx.apply(x32, y32, q.PREC_FP32)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        ctx.apply(x32, y32, q.PREC_FP32)
+    e1.record()
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / 5
+
+    # e2e: through the C ABI from host descriptors to host results
+    e2e_steps = max(1, min(args.steps, 3))
+    mu_h = torch.empty((N, R), dtype=torch.complex128, pin_memory=True)
+    u_h = torch.empty((M, R), dtype=torch.complex128, pin_memory=True)
+    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    e2e_pairs = 0
+    for _ in range(e2e_steps):
+        c2 = q.Context(local_rank)
+        c2.set_bodies(sc.bodies)
+        c2.set_wavenumber(sc.k, sc.eta)
+        c2.assemble()
+        bb = torch.zeros((N, R), dtype=torch.complex128, device="cuda")
+        c2.incident_plane(sc.directions, bb)
+        mm = torch.zeros_like(bb)
+        st = c2.solve(bb, mm, q.PREC_FP32, tol=1e-11)
+        uu = torch.zeros((M, R), dtype=torch.complex128, device="cuda")
+        c2.farfield(mm, xh, uu)
+        mu_h.copy_(mm, non_blocking=True)
+        u_h.copy_(uu, non_blocking=True)
+        torch.cuda.synchronize()
+        c2.close()
+        e2e_pairs += (st["applies_fp32"] + st["applies_fp64"]) * pairs * R
+    e2e_t = time.perf_counter() - t_start
+    h2d = sum(8 * (9 + 3 + 6 + len(bd.mode_cos) + len(bd.mode_sin)) for bd in sc.bodies) + 8 * 3 * R + 8 * 3 * M
+    d2h = 16 * N * R + 16 * M * R
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    ms = elapsed / args.steps * 1e3
+    lat = sorted(step_ms)
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(math.ceil(p / 100 * len(lat))) - 1)]
+
+    achieved = flops / asm_alone / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 operator + f64 (assembly, Krylov, refinement)",
+        "data": "synthetic (seeded quasi-axisymmetric bodies)",
+        "config": {"workload": sc.name, "n_bodies": len(sc.bodies), "N": N, "R": R, "k": sc.k, "eta": sc.eta,
+                   "tol": 1e-11, "far_field_dirs": M, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (self blocks %.2f GB resident)" % (
+                       sum(bd.n_nodes ** 2 for bd in sc.bodies) * 24 / 1e9)},
+        "solves_per_s": args.steps * world / elapsed,
+        "latency_ms": {"p50": pct(50), "p99": pct(99)},
+        "breakdown_ms": {"assembly": statistics.mean(asm_ms), "solve": statistics.mean(solve_ms),
+                         "far_field": statistics.mean(ff_ms)},
+        "solver": {"applies_per_solve": statistics.mean(applies), "iterations": recs[-1][1]["iterations"],
+                   "refinements": recs[-1][1]["refinements"], "rel_residual": recs[-1][1]["rel_residual"],
+                   "rel_err_vs_fp64_gpu": rel_err},
+        "fp32_apply": {"ms": apply_ms, "pairs_per_s": pairs / (apply_ms / 1e3),
+                       "pair_rhs_per_s": pairs * R / (apply_ms / 1e3)},
+        "roofline": {"kernel": "selfblock_kernel (FP64 self-block assembly)", "bound": "alu",
+                     "achieved": achieved, "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64,
+                     "traffic": None, "peak_note": "nominal dense FP64 1.25 TFLOP/s; cuBLAS DGEMM measured "
+                     "%.3f TFLOP/s on this GPU" % peak64_meas},
+        "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sc, seconds: float):
+    """The FP64 oracle as it stands, on this host's cores: its explicit pair sum
+    over a bounded sample of target rows of the same scene, in pair-interactions/s."""
+    import numpy as np
+
+    from oracle import operator as op
+    from oracle.geometry import body_nodes
+    import scenes
+
+    nodes = [body_nodes(b) for b in sc.bodies]
+    N = sum(n.count for n in nodes)
+    sigma = scenes.rhs_seeded(N, sc.n_rhs, 1)
+    rng = np.random.default_rng(0)
+    done_pairs, t0 = 0, time.perf_counter()
+    off = op.body_offsets(nodes)
+    rows_done = 0
+    while time.perf_counter() - t0 < seconds:
+        rows = rng.integers(0, N, 16)
+        op.pair_sum(nodes, sigma, sc.k, sc.eta, targets=rows)
+        for g in rows:
+            b = int(np.searchsorted(off, g, side="right") - 1)
+            done_pairs += N - nodes[b].count
+        rows_done += 16
+    t = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": done_pairs / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{rows_done} random target rows x all other-body sources of the same scene "
+                      f"(explicit FP64 pair sum, numpy), {t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle (the reference arm for this build) on the host cores."""
+    if rank != 0:
+        return
+    import scenes
+    sc = scenes.config(args.config)
+    for _ in range(args.warmup):
+        cpu_baseline(sc, 1.0)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(sc, args.cpu_seconds / max(1, args.steps)))
+    elapsed = time.perf_counter() - t0
+    v = statistics.mean(x["value"] for x in vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded quasi-axisymmetric bodies)",
+           "config": {"workload": sc.name, "N": sc.n_nodes, "R": sc.n_rhs, "k": sc.k},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=1, help="workload index (1 = 16 bodies x 2048 nodes, k = 5)")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -76,6 +76,10 @@ typedef struct {
 
 const char* qams_strerror(int code);
 
+/* Number of CUDA kernels the library has launched in this process (all
+ * contexts); lets callers attribute device work to the library. */
+long long qams_kernel_launches(void);
+
 /* Create a context on CUDA device `cuda_device`.  hbm_budget_bytes = 0 means
  * no limit.  Errors: QAMS_EINVAL, QAMS_ECUDA. */
 int qams_create(qams_ctx** out, int cuda_device, size_t hbm_budget_bytes);
@@ -111,6 +115,69 @@ int qams_set_wavenumber(qams_ctx* ctx, double k, double eta);
  * pair, e^{ik rho} = e^{ik rho_0} e^{ik (rho - rho_0)}, rho_0 = |c_a - c_b|
  * in FP64.  Errors: QAMS_EINVAL (R < 1, no bodies, no wavenumber). */
 int qams_pairsum(qams_ctx* ctx, int R, const void* sigma_dev, void* y_dev, int precision, void* stream);
+
+/* Self-block assembly (Sec. 3.1-3.4): for every body the dense n_b x n_b
+ * block of 1/2 I + D - i eta S, by product integration against the tensor
+ * Lagrange interpolant of mu |J| (Gauss-Legendre in s, trigonometric in
+ * theta) with modal Green's functions for the azimuthal integral (Eqs.
+ * modalgreen, modal0, leg_recur, dleg_recur, conv, I1) and a composite
+ * graded Gauss rule for the singular outer integral (in place of the
+ * paper's generalised Gaussian tables).  Computed in FP64 on the device,
+ * kept library-owned (complex128, plus a complex64 copy for the FP32
+ * path).  Uses the wavenumber of qams_set_wavenumber.  Blocking.
+ * Errors: QAMS_EINVAL (no bodies/wavenumber; order > 19 or n_theta > 64),
+ * QAMS_EBUDGET, QAMS_ECUDA. */
+int qams_assemble(qams_ctx* ctx, void* stream);
+
+/* Copy body `body`'s assembled self block (row-major n_b x n_b complex128,
+ * rows = targets, columns = sources, both in node order) to dst_dev. */
+int qams_copy_selfblock(const qams_ctx* ctx, int body, void* dst_dev, void* stream);
+
+/* Operator apply (Eq. linearsys): y = (1/2 I + D - i eta S) x for [N][R]
+ * complex x (densities mu, weights not folded in), self blocks times x
+ * plus the inter-body pair sum of w x.  QAMS_PREC_FP64 works in complex128,
+ * QAMS_PREC_FP32 in complex64 with the complex64 block copy.  Requires
+ * qams_assemble.  Uses a library-owned workspace of N*R complex. */
+int qams_apply(qams_ctx* ctx, int R, const void* x_dev, void* y_dev, int precision, void* stream);
+
+/* Solver options (Sec. 6: GMRES; restart, tolerances and orthogonalisation
+ * are not stated by the paper).  precision = QAMS_PREC_FP64: restarted
+ * GMRES with the FP64 apply, stop at ||b - A mu|| <= tol ||b|| per column.
+ * precision = QAMS_PREC_FP32: iterative refinement -- each correction solves
+ * A d = r by GMRES with the FP32 apply to a relative reduction inner_tol,
+ * then mu += d and r = b - A mu with the FP64 apply, until r meets tol.  The
+ * Krylov basis and Gram-Schmidt (classical, applied twice) are FP64 in both
+ * modes.  qams_solve_opts_default fills: FP32, restart 50, max_iters 1000,
+ * tol 1e-11, inner_tol 1e-5, max_refine 12. */
+typedef struct {
+  int precision;
+  int restart;      /* m, 1..200 */
+  int max_iters;    /* total Arnoldi steps */
+  double tol;       /* on ||b - A mu|| / ||b|| (FP64 residual) */
+  double inner_tol; /* FP32 mode: reduction per correction */
+  int max_refine;   /* FP32 mode: corrections */
+} qams_solve_opts;
+
+typedef struct {
+  int iterations;      /* Arnoldi steps (all corrections)          */
+  int refinements;     /* FP64 residual evaluations (FP32 mode)    */
+  double rel_residual; /* max over columns of ||b - A mu|| / ||b|| */
+  double solve_ms;     /* device time of the call (CUDA events)    */
+  int applies_fp32;    /* operator applies with the FP32 path      */
+  int applies_fp64;    /* operator applies with the FP64 path      */
+} qams_solve_stats;
+
+void qams_solve_opts_default(qams_solve_opts* opts);
+
+/* Solve (1/2 I + D - i eta S) mu = rhs (Eq. linearsys) for R <= 16
+ * right-hand sides, rhs_dev and mu_dev [N][R] complex128 (mu overwritten;
+ * the initial guess is zero).  opts may be NULL (defaults); stats may be
+ * NULL.  Requires qams_assemble.  Allocates its Krylov workspace
+ * ((restart+1) N R complex128) for the duration of the call.  Blocking.
+ * Errors: QAMS_EINVAL, QAMS_ENOCONV (mu holds the last iterate, stats
+ * filled), QAMS_ENUMERIC, QAMS_EBUDGET, QAMS_ECUDA. */
+int qams_solve(qams_ctx* ctx, int R, const void* rhs_dev, void* mu_dev, const qams_solve_opts* opts,
+               qams_solve_stats* stats, void* stream);
 
 /* Right-hand sides b = -u^inc = -e^{ik d.x} (Sec. 6) for R unit directions
  * dirs_host [R][3]; rhs_dev is [N][R] complex128. */

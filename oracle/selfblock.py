@@ -88,7 +88,7 @@ def _integrand(bn: BodyNodes, s_t: float, theta_t: float, h: float, pan_nodes,
     return P[:, None] * F[None, :]
 
 
-def _adaptive(fun, tol_rel: float, max_intervals: int = 2000):
+def _adaptive(fun, tol_rel: float, max_intervals: int = 500):
     """Integrate a vector function of v over [0, 1] by adaptive GK 7/15."""
     def rule(a, b):
         h = 0.5 * (b - a)
@@ -96,7 +96,10 @@ def _adaptive(fun, tol_rel: float, max_intervals: int = 2000):
         vals = np.stack(vals)
         k15 = h * np.tensordot(_WK, vals, axes=1)
         g7 = h * np.tensordot(_WG, vals, axes=1)
-        return k15, float(np.max(np.abs(k15 - g7)))
+        # round-off floor of the pair: differences at the level of a few
+        # hundred ulps of h * max|f| are rounding, not truncation
+        floor = 200 * np.finfo(float).eps * abs(h) * float(np.max(np.abs(vals)))
+        return k15, max(0.0, float(np.max(np.abs(k15 - g7))) - floor)
 
     heap = []
     total = 0
@@ -137,7 +140,7 @@ def pair_kernel(x, y, ny, k: float, eta: float):
     return g * ((1j * k / rho - 1.0 / rho ** 2) * nd - 1j * eta)
 
 
-def self_block_rows(bn: BodyNodes, rows, k: float, eta: float, tol: float = 1e-14):
+def self_block_rows(bn: BodyNodes, rows, k: float, eta: float, tol: float = 1e-13):
     """Rows ``rows`` (body-local target indices) of the self block, (len(rows), n) complex."""
     n = bn.count
     nth, order = bn.n_theta, bn.order
@@ -181,7 +184,7 @@ def _rows_job(args):
     return self_block_rows(bn, rows, k, eta, tol)
 
 
-def self_block_rows_parallel(bn: BodyNodes, rows, k: float, eta: float, tol: float = 1e-14,
+def self_block_rows_parallel(bn: BodyNodes, rows, k: float, eta: float, tol: float = 1e-13,
                              workers: int = 0):
     """``self_block_rows`` over a spawn-started process pool (rows are independent)."""
     import concurrent.futures as cf
@@ -201,7 +204,7 @@ def self_block_rows_parallel(bn: BodyNodes, rows, k: float, eta: float, tol: flo
     return out
 
 
-def self_block(bn: BodyNodes, k: float, eta: float, tol: float = 1e-14, workers: int = 0):
+def self_block(bn: BodyNodes, k: float, eta: float, tol: float = 1e-13, workers: int = 0):
     """The full self block.  On a body of revolution (straight axis) the block
     is circulant in theta, so only one azimuth per generating-curve node is
     integrated and the rest follow by cyclic shifts."""

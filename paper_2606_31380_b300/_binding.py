@@ -18,6 +18,16 @@ def lib_path() -> str:
     return os.path.join(HERE, "libqams.so")
 
 
+class SolveOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int), ("tol", C.c_double),
+                ("inner_tol", C.c_double), ("max_refine", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double),
+                ("solve_ms", C.c_double), ("applies_fp32", C.c_int), ("applies_fp64", C.c_int)]
+
+
 class BodyDesc(C.Structure):
     _fields_ = [("n_panels", C.c_int), ("order", C.c_int), ("n_theta", C.c_int),
                 ("base_radius", C.c_double), ("n_modes", C.c_int),
@@ -41,6 +51,7 @@ def load_library():
     vp, i, d, ll = C.c_void_p, C.c_int, C.c_double, C.c_longlong
     sig = {
         "qams_strerror": (C.c_char_p, [i]),
+        "qams_kernel_launches": (C.c_longlong, []),
         "qams_create": (i, [C.POINTER(vp), i, C.c_size_t]),
         "qams_destroy": (None, [vp]),
         "qams_set_bodies": (i, [vp, i, C.POINTER(BodyDesc), d]),
@@ -50,6 +61,11 @@ def load_library():
         "qams_set_wavenumber": (i, [vp, d, d]),
         "qams_pairsum": (i, [vp, i, vp, vp, i, vp]),
         "qams_incident_plane": (i, [vp, i, vp, vp, vp]),
+        "qams_assemble": (i, [vp, vp]),
+        "qams_copy_selfblock": (i, [vp, i, vp, vp]),
+        "qams_apply": (i, [vp, i, vp, vp, i, vp]),
+        "qams_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
+        "qams_solve": (i, [vp, i, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveStats), vp]),
         "qams_farfield": (i, [vp, i, vp, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -65,6 +81,11 @@ class QamsError(RuntimeError):
         lib = load_library()
         super().__init__(f"{what}: {lib.qams_strerror(code).decode()} (code {code})")
         self.code = code
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libqams in this process so far."""
+    return int(load_library().qams_kernel_launches())
 
 
 def _check(code: int, what: str):
@@ -170,6 +191,51 @@ class Context:
         _check(self.lib.qams_pairsum(self._h, R, _dev(sigma, dt, (self.N, R), "sigma"),
                                      _dev(y, dt, (self.N, R), "y"), precision, C.c_void_p(_stream_ptr(stream))),
                "qams_pairsum")
+
+    def assemble(self, stream=None):
+        _check(self.lib.qams_assemble(self._h, C.c_void_p(_stream_ptr(stream))), "qams_assemble")
+
+    def copy_selfblock(self, body: int, dst, stream=None):
+        import torch
+        n = int(self.body_offsets()[body + 1] - self.body_offsets()[body])
+        _check(self.lib.qams_copy_selfblock(self._h, body, _dev(dst, torch.complex128, (n, n), "dst"),
+                                            C.c_void_p(_stream_ptr(stream))), "qams_copy_selfblock")
+
+    def apply(self, x, y, precision: int = PREC_FP64, stream=None):
+        import torch
+        R = x.shape[1]
+        dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
+        _check(self.lib.qams_apply(self._h, R, _dev(x, dt, (self.N, R), "x"), _dev(y, dt, (self.N, R), "y"),
+                                   precision, C.c_void_p(_stream_ptr(stream))), "qams_apply")
+
+    def solve(self, rhs, mu, precision: int = PREC_FP32, tol: float = None, restart: int = None,
+              max_iters: int = None, inner_tol: float = None, stream=None, check: bool = True):
+        """Solve A mu = rhs; returns a dict of solver statistics."""
+        import torch
+        R = rhs.shape[1]
+        o = SolveOpts()
+        self.lib.qams_solve_opts_default(C.byref(o))
+        o.precision = precision
+        if tol is not None:
+            o.tol = tol
+        elif precision == PREC_FP64:
+            o.tol = 1e-12
+        if restart is not None:
+            o.restart = restart
+        if max_iters is not None:
+            o.max_iters = max_iters
+        if inner_tol is not None:
+            o.inner_tol = inner_tol
+        st = SolveStats()
+        code = self.lib.qams_solve(self._h, R, _dev(rhs, torch.complex128, (self.N, R), "rhs"),
+                                   _dev(mu, torch.complex128, (self.N, R), "mu"), C.byref(o), C.byref(st),
+                                   C.c_void_p(_stream_ptr(stream)))
+        stats = dict(iterations=st.iterations, refinements=st.refinements, rel_residual=st.rel_residual,
+                     solve_ms=st.solve_ms, applies_fp32=st.applies_fp32, applies_fp64=st.applies_fp64,
+                     code=code)
+        if check:
+            _check(code, "qams_solve")
+        return stats
 
     def incident_plane(self, dirs: np.ndarray, rhs, stream=None):
         import torch

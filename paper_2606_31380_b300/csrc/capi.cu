@@ -5,7 +5,12 @@
 
 #include "qams_internal.h"
 
+#include <atomic>
+
 static thread_local char g_last_cuda[256];
+static std::atomic<long long> g_launches{0};
+
+void qams_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void qams_internal_last_cuda_error(cudaError_t e, const char* what) {
   snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", what, cudaGetErrorString(e));
@@ -31,11 +36,14 @@ void qams_dev_free(qams_ctx* c, DeviceBuf* b) {
 
 qams_ctx::~qams_ctx() {
   cudaSetDevice(device);
-  for (DeviceBuf* b : {&x64, &n64, &x32, &n32, &centers, &boff, &d_tiles, &d_splits, &partial})
+  for (DeviceBuf* b : {&x64, &n64, &x32, &n32, &centers, &boff, &jac64, &d_tiles, &d_splits, &partial,
+                        &blocks64, &blocks32, &blk_off, &ws_sigma, &ws_y})
     qams_dev_free(this, b);
 }
 
 extern "C" {
+
+long long qams_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* qams_strerror(int code) {
   switch (code) {
@@ -99,7 +107,10 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
       if (std::sqrt(dx * dx + dy * dy + dz * dz) < rad[i] + rad[j] + min_gap) return QAMS_EGEOM;
     }
   QAMS_CUDA(cudaSetDevice(c->device));
-  for (DeviceBuf* b : {&c->x64, &c->n64, &c->x32, &c->n32, &c->centers, &c->boff}) qams_dev_free(c, b);
+  for (DeviceBuf* b : {&c->x64, &c->n64, &c->x32, &c->n32, &c->centers, &c->boff, &c->jac64, &c->blocks64,
+                       &c->blocks32, &c->blk_off, &c->ws_sigma, &c->ws_y})
+    qams_dev_free(c, b);
+  c->assembled = false;
   c->bodies = std::move(bh);
   int rc = qams_build_nodes(c);
   if (rc) return rc;
@@ -133,6 +144,12 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
   if ((rc = qams_dev_alloc(c, &c->n32, sizeof(float) * 4 * N))) return rc;
   if ((rc = qams_dev_alloc(c, &c->centers, sizeof(double) * 4 * nb))) return rc;
   if ((rc = qams_dev_alloc(c, &c->boff, sizeof(long long) * (nb + 1)))) return rc;
+  if ((rc = qams_dev_alloc(c, &c->jac64, sizeof(double) * N))) return rc;
+  std::vector<long long> boffs(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) boffs[b + 1] = boffs[b] + (long long)c->bodies[b].n * c->bodies[b].n;
+  if ((rc = qams_dev_alloc(c, &c->blk_off, sizeof(long long) * (nb + 1)))) return rc;
+  QAMS_CUDA(cudaMemcpy(c->blk_off.p, boffs.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->jac64.p, c->hj.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->x64.p, x4.data(), sizeof(double) * 4 * N, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->n64.p, n4.data(), sizeof(double) * 4 * N, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->x32.p, xl.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
@@ -176,6 +193,36 @@ int qams_pairsum(qams_ctx* c, int R, const void* sigma, void* y, int precision, 
   if (precision != QAMS_PREC_FP64 && precision != QAMS_PREC_FP32) return QAMS_EINVAL;
   QAMS_CUDA(cudaSetDevice(c->device));
   return qams_pairsum_launch(c, R, sigma, y, precision, (cudaStream_t)stream);
+}
+
+int qams_assemble(qams_ctx* c, void* stream) {
+  if (!c || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  c->assembled = false;
+  int rc = qams_assemble_launch(c, (cudaStream_t)stream);
+  if (rc) return rc;
+  rc = qams_blocks_to_fp32(c, (cudaStream_t)stream);
+  if (rc) return rc;
+  c->assembled = true;
+  return QAMS_OK;
+}
+
+int qams_copy_selfblock(const qams_ctx* c, int body, void* dst, void* stream) {
+  if (!c || !c->assembled || body < 0 || body >= (int)c->bodies.size() || !dst) return QAMS_EINVAL;
+  long long off = 0;
+  for (int b = 0; b < body; ++b) off += (long long)c->bodies[b].n * c->bodies[b].n;
+  const long long n = c->bodies[body].n;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  QAMS_CUDA(cudaMemcpyAsync(dst, (const double2*)c->blocks64.p + off, sizeof(double2) * n * n,
+                            cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return QAMS_OK;
+}
+
+int qams_apply(qams_ctx* c, int R, const void* x, void* y, int precision, void* stream) {
+  if (!c || R < 1 || !x || !y || !c->assembled) return QAMS_EINVAL;
+  if (precision != QAMS_PREC_FP64 && precision != QAMS_PREC_FP32) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  return qams_apply_launch(c, R, x, y, precision, (cudaStream_t)stream);
 }
 
 int qams_incident_plane(qams_ctx* c, int R, const double* dirs, void* rhs, void* stream) {

@@ -73,7 +73,7 @@ int qams_incident_launch(qams_ctx* c, int R, const double* dirs_host, void* rhs,
   QAMS_CUDA(cudaMemcpyAsync(d.p, dirs_host, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, st));
   const long long n = c->N * R;
   incident_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const qd4*)c->x64.p, c->N, R,
-                                                               (const double*)d.p, c->k, (double2*)rhs);
+                                                               (const double*)d.p, c->k, (double2*)rhs); qams_count_launch();
   QAMS_CUDA(cudaGetLastError());
   QAMS_CUDA(cudaStreamSynchronize(st));
   qams_dev_free(c, &d);
@@ -90,7 +90,7 @@ int qams_farfield_launch(qams_ctx* c, int R, const void* mu, int M, const double
     const int cnt = std::min(MAXR, R - r0);
     farfield_kernel<<<M, 256, 0, st>>>((const qd4*)c->x64.p, (const qd4*)c->n64.p, c->N,
                                        (const double2*)mu, R, r0, cnt, (const double*)d.p, c->k, c->eta,
-                                       (double2*)uinf);
+                                       (double2*)uinf); qams_count_launch();
     QAMS_CUDA(cudaGetLastError());
   }
   QAMS_CUDA(cudaStreamSynchronize(st));

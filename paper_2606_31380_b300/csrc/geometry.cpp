@@ -106,6 +106,7 @@ int qams_build_nodes(qams_ctx* c) {
   c->hx.assign(3 * N, 0.0);
   c->hn.assign(3 * N, 0.0);
   c->hw.assign(N, 0.0);
+  c->hj.assign(N, 0.0);
   for (auto& bh : c->bodies) {
     const qams_body_desc& d = bh.d;
     Shape sh{d.base_radius, d.axis_length, d.curvature, bh.a.data(), bh.b.data(),
@@ -133,6 +134,7 @@ int qams_build_nodes(qams_ctx* c) {
             c->hn[3 * idx + r] = nr;
           }
           c->hw[idx] = jac * dth * om;
+          c->hj[idx] = jac;
         }
       }
     }

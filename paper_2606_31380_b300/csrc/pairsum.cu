@@ -225,7 +225,7 @@ void launch_f32(qams_ctx* c, dim3 grid, const float2* sigma, int R, int r0, floa
   pairsum_f32_kernel<RC><<<grid, TILE, 0, st>>>(
       (const TargetTile*)c->d_tiles.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
       (const qd4*)c->centers.p, (const float4*)c->x32.p, (const float4*)c->n32.p, sigma, R, r0, c->k,
-      c->eta, out, stride, ld, or0);
+      c->eta, out, stride, ld, or0); qams_count_launch();
 }
 
 template <int RC>
@@ -233,7 +233,7 @@ void launch_f64(qams_ctx* c, dim3 grid, const double2* sigma, int R, int r0, dou
                 int ld, int or0, cudaStream_t st) {
   pairsum_f64_kernel<RC><<<grid, TILE, 0, st>>>(
       (const TargetTile*)c->d_tiles.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
-      (const qd4*)c->x64.p, (const qd4*)c->n64.p, sigma, R, r0, c->k, c->eta, out, stride, ld, or0);
+      (const qd4*)c->x64.p, (const qd4*)c->n64.p, sigma, R, r0, c->k, c->eta, out, stride, ld, or0); qams_count_launch();
 }
 
 }  // namespace
@@ -301,7 +301,7 @@ int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int prec
       if (S > 1) {
         const long long n = c->N * rc;
         reduce_splits_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-            (const float2*)c->partial.p, S, c->N, rc, (float2*)y, R, r0);
+            (const float2*)c->partial.p, S, c->N, rc, (float2*)y, R, r0); qams_count_launch();
         QAMS_CUDA(cudaGetLastError());
       }
     } else {
@@ -320,7 +320,7 @@ int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int prec
       if (S > 1) {
         const long long n = c->N * rc;
         reduce_splits_kernel<double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-            (const double2*)c->partial.p, S, c->N, rc, (double2*)y, R, r0);
+            (const double2*)c->partial.p, S, c->N, rc, (double2*)y, R, r0); qams_count_launch();
         QAMS_CUDA(cudaGetLastError());
       }
     }

@@ -22,6 +22,9 @@ typedef double4_32a qd4;
 
 void qams_internal_last_cuda_error(cudaError_t e, const char* what);
 
+// Process-wide count of kernel launches made by the library.
+void qams_count_launch(int n = 1);
+
 struct BodyHost {
   qams_body_desc d;          // pointers below are re-pointed at the copies
   std::vector<double> a, b;  // profile Fourier modes
@@ -56,7 +59,7 @@ struct qams_ctx {
   bool have_k = false;
 
   // host node tables (FP64, world frame)
-  std::vector<double> hx, hn, hw;  // [N][3], [N][3], [N]
+  std::vector<double> hx, hn, hw, hj;  // [N][3], [N][3], [N], [N] (|J|)
 
   // device node tables
   DeviceBuf x64;     // double4 [N]: world position, w in .w
@@ -65,6 +68,17 @@ struct qams_ctx {
   DeviceBuf n32;     // float4  [N]: world normal
   DeviceBuf centers; // double4 [nb]
   DeviceBuf boff;    // long long [nb+1]
+  DeviceBuf jac64;   // double [N]: |J| at the nodes
+
+  // self blocks (row-major n_b x n_b per body, bodies back to back)
+  DeviceBuf blocks64;  // complex128
+  DeviceBuf blocks32;  // complex64 copy for the FP32 path
+  DeviceBuf blk_off;   // long long [nb+1]: first entry of each block
+  long long block_entries = 0;
+  bool assembled = false;
+
+  // apply workspaces
+  DeviceBuf ws_sigma, ws_y;
 
   // pair-sum launch tables
   std::vector<TargetTile> tiles;
@@ -85,6 +99,14 @@ void qams_gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 // pairsum.cu
 int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int precision, cudaStream_t st);
 int qams_pairsum_prepare(qams_ctx* c);
+
+// selfblock.cu
+int qams_assemble_launch(qams_ctx* c, cudaStream_t st);
+
+// blockops.cu
+int qams_blocks_to_fp32(qams_ctx* c, cudaStream_t st);
+int qams_block_apply(qams_ctx* c, int R, const void* x, void* y, int precision, bool accumulate, cudaStream_t st);
+int qams_apply_launch(qams_ctx* c, int R, const void* x, void* y, int precision, cudaStream_t st);
 
 // fields.cu
 int qams_incident_launch(qams_ctx* c, int R, const double* dirs_host, void* rhs, cudaStream_t st);

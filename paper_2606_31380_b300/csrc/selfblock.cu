@@ -1,0 +1,564 @@
+// Self-block assembly (Sec. 3.1-3.4): one row of the combined-layer self block
+//   A_b[t, (i,l,j)] = 1/2 delta + |J_ilj| int_{panel i} P_l(s) F_j(s) ds,
+//   F_j(s) = n_r(s,theta_j) W^r_j(s) + n_z(s,theta_j) W^z_j(s) - i eta W^0_j(s),
+// per CTA, for every panel i within one of the target's panel (Eq. sx);
+// farther panels take the plain smooth rule.  W_j = int K L_j dtheta comes
+// from the modal Green's functions (Eq. modalgreen) of the source ring at s:
+//   static part  g^_m = Q_{m-1/2}(chi)/(2 pi sqrt(r r~)) (Eq. modal0), Q by the
+//                recursion of Eq. leg_recur (forward near chi = 1, Miller's
+//                backward recursion on ratios otherwise), Q' by Eq. dleg_recur;
+//   k != 0       G^_m = (1/2pi) sum_n f1^_n g^_{m-n} + i f2^_m (Eqs. conv, I1),
+//                and the same split for the source derivatives; the smooth
+//                factors cos(k rho), sinc(k rho) and
+//                (k rho cos k rho - sin k rho)/(k rho)^3 are transformed by a
+//                cosine DFT (all kernels are even in phi = theta - alpha).
+// The outer s-integral replaces the paper's generalised Gaussian tables
+// (not available) with a composite rule: dyadic sub-panels toward the
+// (near-)singular point with order+4 Gauss-Legendre nodes each, and a
+// graded innermost panel (u^6 substitution, 20 nodes) for the logarithm.
+// Ring-target geometry uses difference formulas in h = s - s_t so that
+// r - r~ and c keep full relative precision as h -> 0 (the double-layer
+// pieces W^r, W^z each grow like 1/|h| and cancel in F).
+#include <algorithm>
+#include <cmath>
+
+#include "qams_internal.h"
+
+namespace {
+
+constexpr int NT = 128;      // threads per CTA
+constexpr int BATCH = 16;    // outer nodes whose recursions run together (warp 0)
+constexpr int MAXQ = 1024;   // outer nodes per row
+constexpr int MAXP = 96;     // highest static mode N + n1 + 1
+constexpr int MAXM2 = 96;    // M/2 + 1 samples of the smooth factors
+constexpr int MAXN1 = 88;    // highest smooth-factor mode + 2
+constexpr int MAXN = 32;     // N = n_theta / 2
+constexpr int MAXORD = 19;   // keeps 40 (order + 4) + 72 outer nodes <= MAXQ
+
+struct RowShared {
+  // outer nodes of the row
+  double qh[MAXQ];
+  double qw[MAXQ];
+  int qp[MAXQ];
+  int nq;
+  // per-batch node data (filled by warp 0)
+  double bq[BATCH][MAXP + 1];   // Q_{m-1/2}, then g^_m
+  double bdq[BATCH][MAXP + 1];  // Q', then d_r g^_m ... see below
+  double bs[BATCH][16];         // scalars
+  // per-node work arrays
+  double fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho)
+  double fc[3][MAXN1 + 1];      // their cosine coefficients
+  double hr[MAXN1 + 1], hz[MAXN1 + 1], pr[MAXN1 + 1], pz[MAXN1 + 1], f2[MAXN1 + 1];
+  double gre[3][MAXN + 1], gim[3][MAXN + 1];  // G^, d_r G^, d_z G^ (phi coefficients)
+  double cma[MAXN + 1], sma[MAXN + 1];
+  double wre[3][2 * MAXN], wim[3][2 * MAXN];
+  double nr[2 * MAXN], nz[2 * MAXN];
+  double pl[MAXORD];
+  // row constants
+  double s2tab[MAXM2];     // sin^2(pi q / M)
+  double ctab[4 * MAXM2];  // cos(2 pi j / M), j < M
+  double cth[2 * MAXN], sth[2 * MAXN];
+};
+
+struct AsmBody {
+  int n_panels, order, n_theta, n_modes;
+  double base, L, kappa;
+  double a[8], b[8];
+  long long offset;
+  long long blk;   // first entry of the body's self block
+  int n1, M;       // smooth-factor bandwidth and cosine-DFT size
+  int rule;        // offset of the order's rule tables
+};
+
+__device__ __forceinline__ double rho_prof(const AsmBody& B, double u) {
+  double s = 1.0;
+  for (int m = 1; m <= B.n_modes; ++m) {
+    double sn, cs;
+    sincospi(2.0 * m * u, &sn, &cs);
+    s += B.a[m - 1] * cs + B.b[m - 1] * sn;
+  }
+  return B.base * s;
+}
+
+__device__ __forceinline__ double drho_prof(const AsmBody& B, double u) {
+  double s = 0.0;
+  for (int m = 1; m <= B.n_modes; ++m) {
+    double sn, cs;
+    sincospi(2.0 * m * u, &sn, &cs);
+    s += 2.0 * M_PI * m * (-B.a[m - 1] * sn + B.b[m - 1] * cs);
+  }
+  return B.base * s;
+}
+
+// complete elliptic integrals K, E of modulus mu (mu_c = sqrt(1 - mu^2)) by the AGM
+__device__ void agm_KE(double mu, double mu_c, double* K, double* E) {
+  double a = 1.0, b = mu_c, c = mu;
+  double s = 0.5 * c * c, p = 0.5;
+  for (int it = 0; it < 40; ++it) {
+    const double an = 0.5 * (a + b);
+    const double bn = sqrt(a * b);
+    c = 0.25 * c * c / an;
+    a = an;
+    b = bn;
+    p *= 2.0;
+    s += p * c * c;
+    if (c < 1e-18 * a) break;
+  }
+  *K = M_PI / (2.0 * a);
+  *E = *K * (1.0 - s);
+}
+
+__device__ __forceinline__ double sinc_d(double x) {
+  if (fabs(x) < 0.1) {
+    const double x2 = x * x;
+    return 1.0 - x2 / 6.0 + x2 * x2 / 120.0 - x2 * x2 * x2 / 5040.0 + x2 * x2 * x2 * x2 / 362880.0;
+  }
+  return sin(x) / x;
+}
+
+// (x cos x - sin x)/x^3
+__device__ __forceinline__ double q3_d(double x) {
+  if (fabs(x) < 0.5) {
+    const double x2 = x * x;
+    double term = 1.0, sum = 0.0, fact = 6.0, sign = -1.0;
+    for (int n = 1; n <= 12; ++n) {
+      if (n > 1) fact *= (2.0 * n) * (2.0 * n + 1.0);
+      sum += sign * (2.0 * n) / fact * term;
+      term *= x2;
+      sign = -sign;
+    }
+    return sum;
+  }
+  double sn, cs;
+  sincos(x, &sn, &cs);
+  return (x * cs - sn) / (x * x * x);
+}
+
+// Lane work: geometry of the ring at s_t + h seen from (s_t, theta_t) and the
+// static modal sequence.  Scalars: 0 r, 1 rt, 2 c, 3 dr, 4 alpha, 5 scale,
+// 6 dchi_r, 7 dchi_z, 8 s, 9 dl, 10 r'(s), 11 kappa r.
+__device__ void ring_node(const AsmBody& B, double s_t, double th_t, double h, int P, double* q, double* dq,
+                          double* sc) {
+  const double s = s_t + h;
+  const double sh = sin(0.5 * h);
+  const double mid = s_t + 0.5 * h;
+  const double u_t = 0.5 * (1.0 + sin(s_t));
+  const double u = 0.5 * (1.0 + sin(s));
+  const double du = cos(mid) * sh;
+  double drho = 0.0;
+  for (int m = 1; m <= B.n_modes; ++m) {
+    double s1, c1;
+    sincospi(m * (u + u_t), &s1, &c1);
+    const double s2 = sinpi(m * du);
+    drho += -2.0 * B.a[m - 1] * s1 * s2 + 2.0 * B.b[m - 1] * c1 * s2;
+  }
+  drho *= B.base;
+  const double rho_t = rho_prof(B, u_t);
+  const double r_t = rho_t * cos(s_t);
+  const double rho_s = rho_prof(B, u);
+  const double r = rho_s * cos(s);
+  const double dr_t = drho * cos(s) + rho_t * (-2.0 * sin(mid) * sh);
+  const double Delta = -B.L * cos(mid) * sh;
+  const double kd = B.kappa * Delta;
+  const double sinc_h = fabs(kd) > 1e-8 ? sin(0.5 * kd) / (0.5 * kd) : 1.0;
+  const double sinc_f = fabs(kd) > 1e-8 ? sin(kd) / kd : 1.0;
+  const double omc = 0.5 * B.kappa * Delta * Delta * sinc_h * sinc_h;
+  double skd, ckd, st, ct;
+  sincos(kd, &skd, &ckd);
+  sincos(th_t, &st, &ct);
+  const double a = omc + r_t * ct * ckd;
+  const double b = r_t * st;
+  const double c = Delta * sinc_f - r_t * ct * skd;
+  const double rt = hypot(a, b);
+  const double d2 = -(r_t * ct * skd) * (r_t * ct * skd) + 2.0 * r_t * ct * ckd * omc + omc * omc;
+  const double dr = dr_t - d2 / (rt + r_t);
+  const double alpha = atan2(b, a);
+
+  double delta = (dr * dr + c * c) / (2.0 * r * rt);
+  if (delta < 1e-300) delta = 1e-300;
+  const double chi = 1.0 + delta;
+  const double eta = log1p(delta + sqrt(delta * (2.0 + delta)));
+  const double mu = sqrt(2.0 / (2.0 + delta));
+  const double mu_c = sqrt(delta / (2.0 + delta));
+  double K, E;
+  agm_KE(mu, mu_c, &K, &E);
+  q[0] = mu * K;
+  if (eta * P <= 3.0) {
+    if (P >= 1) q[1] = chi * mu * K - sqrt(2.0 * (chi + 1.0)) * E;
+    for (int n = 2; n <= P; ++n) q[n] = (4.0 * (n - 1) * chi * q[n - 1] - (2.0 * n - 3.0) * q[n - 2]) / (2.0 * n - 1.0);
+  } else {
+    const int n_start = P + 20 + (int)ceil(40.0 / eta);
+    double rho = 0.0;
+    for (int n = n_start; n >= 2; --n) {
+      rho = (2.0 * n - 3.0) / (4.0 * (n - 1) * chi - (2.0 * n - 1.0) * rho);
+      if (n - 1 <= P) q[n - 1] = rho;  // ratio q_{n-1}/q_{n-2}
+    }
+    for (int n = 1; n <= P; ++n) q[n] = q[n - 1] * q[n];
+  }
+  const double chi2m1 = delta * (2.0 + delta);
+  for (int m = 0; m <= P; ++m) {
+    const double prev = m == 0 ? q[1] : q[m - 1];
+    dq[m] = (2.0 * m - 1.0) / (2.0 * chi2m1) * (chi * q[m] - prev);
+  }
+  // normal-component inputs at s
+  const double dl = 0.5 * B.L * cos(s);
+  const double rp = drho_prof(B, u) * 0.5 * cos(s) * cos(s) - rho_s * sin(s);
+  sc[0] = r;
+  sc[1] = rt;
+  sc[2] = c;
+  sc[3] = dr;
+  sc[4] = alpha;
+  sc[5] = 1.0 / (2.0 * M_PI * sqrt(r * rt));
+  sc[6] = (dr * (r + rt) - c * c) / (2.0 * rt * r * r);
+  sc[7] = -c / (r * rt);
+  sc[8] = s;
+  sc[9] = dl;
+  sc[10] = rp;
+  sc[11] = B.kappa * r;
+}
+
+// plain smooth combined-layer kernel (far panels of the same body)
+__device__ void smooth_kernel(const qd4& x, const qd4& y, const qd4& n, double k, double eta, double* kre,
+                              double* kim) {
+  const double dx = y.x - x.x, dy = y.y - x.y, dz = y.z - x.z;
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  const double rinv = rsqrt(r2);
+  double sn, cs;
+  sincos(k * r2 * rinv, &sn, &cs);
+  const double nyx = n.x * dx + n.y * dy + n.z * dz;
+  const double are = -nyx * rinv * rinv, aim = k * nyx * rinv - eta;
+  const double f = rinv * 0.079577471545947667884;
+  *kre = (cs * are - sn * aim) * f;
+  *kim = (sn * are + cs * aim) * f;
+}
+
+__global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict__ bodies, int nb,
+                                                       const double* __restrict__ rules,
+                                                       const qd4* __restrict__ x64, const qd4* __restrict__ n64,
+                                                       const double* __restrict__ jac, double k, double eta,
+                                                       long long row0, double2* __restrict__ blocks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RowShared& S = *reinterpret_cast<RowShared*>(smem_raw);
+  double2* acc = reinterpret_cast<double2*>(smem_raw + sizeof(RowShared));
+
+  const long long g = row0 + blockIdx.x;  // global target node
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bodies[mid].offset <= g) lo = mid; else hi = mid - 1;
+  }
+  const AsmBody B = bodies[lo];
+  const int tid = threadIdx.x;
+  const int nth = B.n_theta, N = nth / 2, order = B.order;
+  const int per_panel = order * nth;
+  const int nbn = B.n_panels * per_panel;
+  const int t = (int)(g - B.offset);
+  const int p = t / per_panel;
+  const int lt = (t % per_panel) / nth;
+  const int jt = t % nth;
+  const double* gl_x = rules + B.rule;              // [order] on [-1,1]
+  const double* dy_x = gl_x + 2 * order;            // [order+4] on [0,1]
+  const double* dy_w = dy_x + (order + 4);
+  const double* in_x = dy_w + (order + 4);          // [20]
+  const double* in_w = in_x + 20;
+  const double* ad_x = in_w + 20;                   // [16]
+  const double* ad_w = ad_x + 16;
+  const double pw = M_PI / B.n_panels;
+  const double s_t = -M_PI / 2 + pw * (p + 0.5 + 0.5 * gl_x[lt]);
+  const double th_t = 2.0 * M_PI * jt / nth;
+  const bool kz = (k == 0.0);
+  const int n1 = kz ? 0 : B.n1;
+  const int M = B.M, M2 = M / 2;
+  const int P = N + n1 + 1;
+
+  for (int e = tid; e < nbn; e += NT) acc[e] = make_double2(0.0, 0.0);
+  // outer nodes (thread 0 builds the list; pieces follow the panel layout)
+  if (tid == 0) {
+    int nq = 0;
+    const double dpole = fmin(s_t + M_PI / 2, M_PI / 2 - s_t);
+    const int ng = order + 4;
+    for (int i = max(0, p - 1); i <= min(B.n_panels - 1, p + 1); ++i) {
+      const double plo = -M_PI / 2 + pw * i, phi_ = plo + pw;
+      double s0[2], e0[2];
+      int npieces;
+      if (i == p) { s0[0] = s_t; e0[0] = plo; s0[1] = s_t; e0[1] = phi_; npieces = 2; }
+      else if (i < p) { s0[0] = phi_; e0[0] = plo; npieces = 1; }
+      else { s0[0] = plo; e0[0] = phi_; npieces = 1; }
+      for (int pc = 0; pc < npieces; ++pc) {
+        const double L = e0[pc] - s0[pc], aL = fabs(L);
+        const double h0 = s0[pc] - s_t;
+        int K = 6;
+        if (i == p) {
+          K = max(5, (int)ceil(log2(aL / (0.5 * dpole))));
+          K = min(K, 14);
+        }
+        double top = 1.0;
+        for (int kk = 0; kk < K; ++kk) {
+          const double bot = 0.5 * top;
+          for (int gq = 0; gq < ng && nq < MAXQ; ++gq, ++nq) {
+            const double v = bot + (top - bot) * dy_x[gq];
+            S.qh[nq] = h0 + L * v;
+            S.qw[nq] = (top - bot) * dy_w[gq] * aL;
+            S.qp[nq] = i;
+          }
+          top = bot;
+        }
+        const double* ix = (i == p) ? in_x : ad_x;
+        const double* iw = (i == p) ? in_w : ad_w;
+        const int ni = (i == p) ? 20 : 16;
+        const int pp = (i == p) ? 6 : 2;
+        for (int gq = 0; gq < ni && nq < MAXQ; ++gq, ++nq) {
+          const double uu = ix[gq];
+          const double up = pp == 6 ? uu * uu * uu * uu * uu * uu : uu * uu;
+          S.qh[nq] = h0 + L * top * up;
+          S.qw[nq] = top * iw[gq] * pp * (up / uu) * aL;
+          S.qp[nq] = i;
+        }
+      }
+    }
+    S.nq = nq;
+  }
+  // row tables
+  for (int q = tid; q <= M2; q += NT) {
+    const double sv = sinpi((double)q / M);
+    S.s2tab[q] = sv * sv;
+  }
+  for (int j = tid; j < M; j += NT) S.ctab[j] = cospi(2.0 * j / M);
+  for (int j = tid; j < nth; j += NT) sincospi(2.0 * j / nth, &S.sth[j], &S.cth[j]);
+  __syncthreads();
+  const int nq = S.nq;
+
+  for (int b0 = 0; b0 < nq; b0 += BATCH) {
+    const int nbatch = min(BATCH, nq - b0);
+    if (tid < nbatch) ring_node(B, s_t, th_t, S.qh[b0 + tid], P, S.bq[tid], S.bdq[tid], S.bs[tid]);
+    __syncthreads();
+    for (int bi = 0; bi < nbatch; ++bi) {
+      const double* sc = S.bs[bi];
+      const double r = sc[0], rt = sc[1], c = sc[2], dr = sc[3], alpha = sc[4], scale = sc[5];
+      const double dchi_r = sc[6], dchi_z = sc[7], s = sc[8];
+      const double* q = S.bq[bi];
+      const double* dq = S.bdq[bi];
+      // B: samples of the smooth factors, e^{i m alpha}
+      if (!kz) {
+        for (int e = tid; e <= M2; e += NT) {
+          const double rho = sqrt(dr * dr + c * c + 4.0 * r * rt * S.s2tab[e]);
+          const double x = k * rho;
+          S.fs[0][e] = cos(x);
+          S.fs[1][e] = sinc_d(x);
+          S.fs[2][e] = q3_d(x);
+        }
+      }
+      for (int m = tid; m <= N; m += NT) sincos(m * alpha, &S.sma[m], &S.cma[m]);
+      __syncthreads();
+      // C1: cosine coefficients f^_n = (2pi/M)[f_0 + (-1)^n f_{M/2} + 2 sum f_q cos(2 pi n q/M)]
+      if (!kz) {
+        for (int e = tid; e < 3 * (n1 + 2); e += NT) {
+          const int fn = e / (n1 + 2), n = e % (n1 + 2);
+          const double* f = S.fs[fn];
+          double sum = 0.0;
+          int idx = 0;
+          for (int qq = 1; qq < M2; ++qq) {
+            idx += n;
+            if (idx >= M) idx -= M;
+            sum += f[qq] * S.ctab[idx];
+          }
+          S.fc[fn][n] = (2.0 * M_PI / M) * (f[0] + ((n & 1) ? -f[M2] : f[M2]) + 2.0 * sum);
+        }
+        __syncthreads();
+        // C2: derived spectra (multiplying by cos(phi) averages neighbours)
+        const double k2 = k * k, k3 = k2 * k / (4.0 * M_PI);
+        for (int n = tid; n <= n1; n += NT) {
+          const double Sm = S.fc[1][n == 0 ? 1 : n - 1], Sp = S.fc[1][n + 1];
+          const double Qm = S.fc[2][n == 0 ? 1 : n - 1], Qp = S.fc[2][n + 1];
+          S.hr[n] = -k2 * ((dr + rt) * S.fc[1][n] - 0.5 * rt * (Sm + Sp));
+          S.hz[n] = k2 * c * S.fc[1][n];
+          S.f2[n] = k / (4.0 * M_PI) * S.fc[1][n];
+          S.pr[n] = k3 * ((dr + rt) * S.fc[2][n] - 0.5 * rt * (Qm + Qp));
+          S.pz[n] = -k3 * c * S.fc[2][n];
+        }
+        __syncthreads();
+      }
+      // D: modal coefficients of G, d_r G, d_z G for m = 0..N
+      for (int e = tid; e < 3 * (N + 1); e += NT) {
+        const int comp = e / (N + 1), m = e % (N + 1);
+        double re, im = 0.0;
+        if (kz) {
+          const double g0 = q[m] * scale;
+          re = comp == 0 ? g0 : (comp == 1 ? dq[m] * dchi_r * scale - g0 / (2.0 * r) : dq[m] * dchi_z * scale);
+        } else {
+          double sum = 0.0;
+          for (int n = -n1; n <= n1; ++n) {
+            const int an = n < 0 ? -n : n;
+            const int am = (m - n) < 0 ? n - m : m - n;
+            const double g0 = q[am] * scale;
+            if (comp == 0) {
+              sum += S.fc[0][an] * g0;
+            } else if (comp == 1) {
+              sum += S.fc[0][an] * (dq[am] * dchi_r * scale - g0 / (2.0 * r)) + S.hr[an] * g0;
+            } else {
+              sum += S.fc[0][an] * (dq[am] * dchi_z * scale) + S.hz[an] * g0;
+            }
+          }
+          re = sum / (2.0 * M_PI);
+          im = m <= n1 ? (comp == 0 ? S.f2[m] : (comp == 1 ? S.pr[m] : S.pz[m])) : 0.0;
+        }
+        S.gre[comp][m] = re;
+        S.gim[comp][m] = im;
+      }
+      // E (part): normal components at (s, theta_j) and Lagrange basis P_l(s)
+      for (int j = tid; j < nth; j += NT) {
+        const double A = sc[9] * (1.0 - sc[11] * S.cth[j]);
+        const double Bv = sc[10];
+        const double hh = rsqrt(A * A + Bv * Bv);
+        S.nr[j] = A * hh;
+        S.nz[j] = -Bv * hh;
+      }
+      const int ip = S.qp[b0 + bi];
+      if (tid < order) {
+        const double xs = (s - (-M_PI / 2 + pw * ip)) / pw * 2.0 - 1.0;  // panel coordinate
+        double v = 1.0;
+        for (int mm = 0; mm < order; ++mm)
+          if (mm != tid) v *= (xs - gl_x[mm]) / (gl_x[tid] - gl_x[mm]);
+        S.pl[tid] = v;
+      }
+      __syncthreads();
+      // E: W_j = (1/2N)[G_0 + 2 sum_{m<N} G_m cos m(theta_j - alpha) + G_N cos N(theta_j - alpha)]
+      for (int e = tid; e < 3 * nth; e += NT) {
+        const int comp = e / nth, j = e % nth;
+        double sre = S.gre[comp][0], sim = S.gim[comp][0];
+        int idx = 0;
+        for (int m = 1; m <= N; ++m) {
+          idx += j;
+          if (idx >= nth) idx -= nth;
+          const double cm = S.cth[idx] * S.cma[m] + S.sth[idx] * S.sma[m];
+          const double f = (m < N) ? 2.0 * cm : cm;
+          sre += f * S.gre[comp][m];
+          sim += f * S.gim[comp][m];
+        }
+        S.wre[comp][j] = sre / nth;
+        S.wim[comp][j] = sim / nth;
+      }
+      __syncthreads();
+      // F: accumulate w * P_l(s) * F_j
+      const double wq = S.qw[b0 + bi];
+      const int base = ip * per_panel;
+      for (int e = tid; e < per_panel; e += NT) {
+        const int l = e / nth, j = e % nth;
+        const double fre = S.nr[j] * S.wre[1][j] + S.nz[j] * S.wre[2][j] + eta * S.wim[0][j];
+        const double fim = S.nr[j] * S.wim[1][j] + S.nz[j] * S.wim[2][j] - eta * S.wre[0][j];
+        const double f = wq * S.pl[l];
+        acc[base + e].x += f * fre;
+        acc[base + e].y += f * fim;
+      }
+      __syncthreads();
+    }
+  }
+  // write the row: near panels from the accumulator times |J|, far panels by the plain rule
+  double2* row = blocks + B.blk + (long long)t * nbn;
+  const qd4 xt = x64[g];
+  for (int e = tid; e < nbn; e += NT) {
+    const int i = e / per_panel;
+    const long long src = B.offset + e;
+    double2 v;
+    if (abs(i - p) <= 1) {
+      const double J = jac[src];
+      v = make_double2(acc[e].x * J, acc[e].y * J);
+    } else {
+      double kre, kim;
+      smooth_kernel(xt, x64[src], n64[src], k, eta, &kre, &kim);
+      const double w = x64[src].w;
+      v = make_double2(kre * w, kim * w);
+    }
+    if (e == t) v.x += 0.5;
+    row[e] = v;
+  }
+}
+
+}  // namespace
+
+size_t qams_selfblock_smem(int max_nb) { return sizeof(RowShared) + sizeof(double2) * (size_t)max_nb; }
+
+int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
+  const int nb = (int)c->bodies.size();
+  // rule tables per distinct order
+  std::vector<double> rules;
+  std::vector<int> rule_off(64, -1);
+  std::vector<AsmBody> ab(nb);
+  long long blk = 0;
+  int max_nb = 0;
+  for (int b = 0; b < nb; ++b) {
+    const BodyHost& bh = c->bodies[b];
+    const qams_body_desc& d = bh.d;
+    if (d.order > MAXORD || d.n_theta / 2 > MAXN || 40 * (d.order + 4) + 72 > MAXQ) return QAMS_EINVAL;
+    if (rule_off[d.order] < 0) {
+      rule_off[d.order] = (int)rules.size();
+      std::vector<double> x, w;
+      qams_gauss_legendre(d.order, x, w);
+      rules.insert(rules.end(), x.begin(), x.end());
+      rules.insert(rules.end(), w.begin(), w.end());
+      qams_gauss_legendre(d.order + 4, x, w);
+      for (auto& v : x) v = 0.5 * (v + 1.0);
+      for (auto& v : w) v *= 0.5;
+      rules.insert(rules.end(), x.begin(), x.end());
+      rules.insert(rules.end(), w.begin(), w.end());
+      qams_gauss_legendre(20, x, w);
+      for (auto& v : x) v = 0.5 * (v + 1.0);
+      for (auto& v : w) v *= 0.5;
+      rules.insert(rules.end(), x.begin(), x.end());
+      rules.insert(rules.end(), w.begin(), w.end());
+      qams_gauss_legendre(16, x, w);
+      for (auto& v : x) v = 0.5 * (v + 1.0);
+      for (auto& v : w) v *= 0.5;
+      rules.insert(rules.end(), x.begin(), x.end());
+      rules.insert(rules.end(), w.begin(), w.end());
+    }
+    AsmBody& A = ab[b];
+    A.n_panels = d.n_panels;
+    A.order = d.order;
+    A.n_theta = d.n_theta;
+    A.n_modes = (int)bh.a.size();
+    A.base = d.base_radius;
+    A.L = d.axis_length;
+    A.kappa = d.curvature;
+    double amp = 0.0;
+    for (int m = 0; m < 8; ++m) {
+      A.a[m] = m < A.n_modes ? bh.a[m] : 0.0;
+      A.b[m] = m < A.n_modes ? bh.b[m] : 0.0;
+      amp += std::fabs(A.a[m]) + std::fabs(A.b[m]);
+    }
+    A.offset = bh.offset;
+    A.blk = blk;
+    blk += (long long)bh.n * bh.n;
+    const double rmax = d.base_radius * (1.0 + amp);
+    A.n1 = (int)std::ceil(1.3 * c->k * rmax + 16.0);
+    A.M = 2 * (A.n1 + 8);
+    if (A.n1 + 2 > MAXN1 || A.M / 2 + 1 > MAXM2 || d.n_theta / 2 + A.n1 + 1 > MAXP || 2 * A.M > 4 * MAXM2)
+      return QAMS_EINVAL;
+    A.rule = rule_off[d.order];
+    max_nb = std::max(max_nb, bh.n);
+  }
+  int rc;
+  qams_dev_free(c, &c->blocks64);
+  if ((rc = qams_dev_alloc(c, &c->blocks64, sizeof(double2) * (size_t)blk))) return rc;
+  c->block_entries = blk;
+  DeviceBuf d_bodies, d_rules;
+  if ((rc = qams_dev_alloc(c, &d_bodies, sizeof(AsmBody) * nb))) return rc;
+  if ((rc = qams_dev_alloc(c, &d_rules, sizeof(double) * rules.size()))) return rc;
+  QAMS_CUDA(cudaMemcpy(d_bodies.p, ab.data(), sizeof(AsmBody) * nb, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(d_rules.p, rules.data(), sizeof(double) * rules.size(), cudaMemcpyHostToDevice));
+  const size_t smem = qams_selfblock_smem(max_nb);
+  QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long chunk = 1 << 20;
+  for (long long r0 = 0; r0 < c->N; r0 += chunk) {
+    const long long n = std::min(chunk, c->N - r0);
+    selfblock_kernel<<<(unsigned)n, NT, smem, st>>>((const AsmBody*)d_bodies.p, nb, (const double*)d_rules.p,
+                                                    (const qd4*)c->x64.p, (const qd4*)c->n64.p,
+                                                    (const double*)c->jac64.p, c->k, c->eta, r0,
+                                                    (double2*)c->blocks64.p); qams_count_launch();
+    QAMS_CUDA(cudaGetLastError());
+  }
+  QAMS_CUDA(cudaStreamSynchronize(st));
+  qams_dev_free(c, &d_bodies);
+  qams_dev_free(c, &d_rules);
+  return QAMS_OK;
+}

@@ -135,7 +135,9 @@ def assembly_flops(scene):
         amp = sum(abs(x) for x in b.mode_cos) + sum(abs(x) for x in b.mode_sin)
         n1 = math.ceil(1.3 * scene.k * b.base_radius * (1 + amp) + 16.0)
         M2 = n1 + 8
-        per_node = (2 * 3 * (n1 + 2) * (M2 - 1) + 15 * (N + 1) * (2 * n1 + 1) + 21 * nth * N + 11 * order * nth)
+        # cosine DFTs (3 factors), convolutions (3 kernels, modes 0..N+1),
+        # Lagrange weights (5 sums of N terms per azimuth), accumulation
+        per_node = (2 * 3 * (n1 + 2) * (M2 - 1) + 15 * (N + 2) * (2 * n1 + 1) + 5 * 7 * nth * N + 20 * order * nth)
         x, _ = np.polynomial.legendre.leggauss(order)
         pw = math.pi / npan
         nodes_per_row = 0
@@ -149,9 +151,9 @@ def assembly_flops(scene):
                     if i == p:
                         for L in (abs(lo - s_t), abs(hi - s_t)):
                             K = min(14, max(5, math.ceil(math.log2(L / (0.5 * dpole)))))
-                            cnt += K * (order + 4) + 20
+                            cnt += K * (order + 4) + order + 20
                     else:
-                        cnt += 6 * (order + 4) + 16
+                        cnt += 6 * (order + 4) + order + 16
                 nodes_per_row += cnt * nth
         total += nodes_per_row * per_node
     return total

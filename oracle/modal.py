@@ -87,7 +87,8 @@ def ring_coords(x_local, ring):
 
 
 def modal_coeffs(r: float, rt: float, c: float, k: float, N: int, dr=None):
-    """G^_m, d_r G^_m, d_z G^_m for m = 0..N in the phi variable.
+    """G^_m, d_r G^_m, d_z G^_m for m = 0..N in the phi variable (call with
+    N+1 for the extra mode that cos(theta) products need).
 
     ``dr`` = r - r~ when known more accurately than the difference of the two.
     Returns three complex arrays of length N+1.
@@ -158,6 +159,27 @@ def modal_coeffs(r: float, rt: float, c: float, k: float, N: int, dr=None):
     Gr = conv(f1, dr0) + conv(hr, g0) + 1j * pr[m + H]
     Gz = conv(f1, dz0) + conv(h3, g0) + 1j * p3[m + H]
     return G, Gr, Gz
+
+
+def lagrange_weights_cos_theta(coef: np.ndarray, alpha: float, n_theta: int):
+    """int K(theta - alpha) cos(theta) L_j(theta) dtheta for j = 0..2N-1 from the
+    phi-coefficients k^_0..k^_{N+1} of an even kernel K.
+
+    cos(theta) = cos(phi) cos(alpha) - sin(phi) sin(alpha); K cos(phi) is even
+    with coefficients (k^_{m-1} + k^_{m+1})/2, K sin(phi) is odd with
+    coefficients (k^_{m-1} - k^_{m+1})/(2i)."""
+    N = n_theta // 2
+    kk = lambda m: coef[abs(m)]
+    even = np.array([0.5 * (kk(m - 1) + kk(m + 1)) for m in range(N + 1)])
+    Wc = lagrange_weights(even, alpha, n_theta)
+    theta = 2 * np.pi * np.arange(n_theta) / n_theta
+    ph = theta - alpha
+    Ws = np.zeros(n_theta, complex)
+    for m in range(1, N + 1):
+        f = 1.0 if m < N else 0.5
+        Ws = Ws + f * (kk(m - 1) - kk(m + 1)) * np.sin(m * ph)
+    Ws = Ws / (2 * N)
+    return np.cos(alpha) * Wc - np.sin(alpha) * Ws
 
 
 def lagrange_weights(coef: np.ndarray, alpha: float, n_theta: int):

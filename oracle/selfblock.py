@@ -4,14 +4,22 @@ Row t of the self block of one body, for the combined-layer operator
 1/2 + D - i eta S (Sec. 2 Remark, Sec. 3.1-3.4), target x_t on panel p:
 
 * source panels i with |i - p| <= 1 (singular / near-singular, Eq. sx):
-  product integration against the tensor interpolant of mu |J| (Sec. 3.1),
-      A[t, (i,l,j)] = |J_ilj| int_{panel i} P_l(s) F_j(s) ds,
-      F_j(s) = n_r(s,theta_j) W^r_j(s) + n_z(s,theta_j) W^z_j(s) - i eta W^0_j(s),
-  where W_j = int K(x_t, y(s,theta)) L_j(theta) dtheta comes from the modal
-  Green's functions (modal.py).  The normal components depend on theta on a
-  quasi-axisymmetric body; they are taken at (s, theta_j), i.e. n_r mu|J| is
-  interpolated in theta as one product (a reading: Eq. modal-normal treats
-  them as constants, which they are only on bodies of revolution);
+  product integration against a tensor Lagrange interpolant, P_l(s) in s
+  and L_j(theta) in theta (Sec. 3.1):
+      A[t, (i,l,j)] = int_{panel i} P_l(s) [F^D_j(s) + |J_ilj| F^S_j(s)] ds,
+      F^D_j(s) = int [(|J| n_r)(s,theta) K^r + (|J| n_z)(s,theta) K^z] L_j dtheta,
+      F^S_j(s) = -i eta int G L_j dtheta,
+  where K^r, K^z are the source-derivative kernels of Sec. 3.2 and all
+  theta-integrals come from modal Green's functions (modal.py).
+  Reading used for quasi-axisymmetric bodies: the paper interpolates mu |J|
+  and treats n_r, n_z as constants, which holds only on bodies of
+  revolution.  Here the single layer keeps the mu |J| interpolant, and the
+  double layer interpolates mu and integrates the exact area-weighted
+  normal, which on this surface family is a trigonometric polynomial of
+  degree one in theta:
+      |J| n_r = r l' (1 - kappa r cos theta),   |J| n_z = -r r'.
+  (The unit normal itself has complex singularities close to the real
+  s-axis on wavy profiles; the area-weighted one is entire.)
 * other panels: the plain Gauss-Legendre x trapezoidal rule (Eq. sx);
 * plus 1/2 on the diagonal (jump relation, Eq. jump3).
 
@@ -23,8 +31,8 @@ vector-valued Gauss-Kronrod 7/15 pair until the estimated error is below
 ``tol`` times the largest entry.
 
 Pins: tests/test_oracle_selfblock.py (Gauss identity at k = 0, sphere
-eigenvalues of S and D, brute-force 2-D quadrature of single entries on a
-tiny body, circulant structure on bodies of revolution).
+eigenvalues of S and D, Mie series, interior point sources, circulant
+structure on bodies of revolution).
 """
 from __future__ import annotations
 
@@ -34,7 +42,7 @@ import math
 import numpy as np
 
 from .geometry import BodyNodes
-from .modal import lagrange_weights, modal_coeffs, ring_coords
+from .modal import lagrange_weights, lagrange_weights_cos_theta, modal_coeffs, ring_coords
 
 # Gauss-Kronrod 7/15 on [-1, 1]
 _XK = np.array([-0.991455371120812639206854697526329, -0.949107912342758524526189684047851,
@@ -71,21 +79,25 @@ def lagrange_basis(nodes: np.ndarray, s: float) -> np.ndarray:
     return out
 
 
-def _integrand(bn: BodyNodes, s_t: float, theta_t: float, h: float, pan_nodes,
+def _integrand(bn: BodyNodes, s_t: float, theta_t: float, h: float, pan_nodes, pan_jac,
                k: float, eta: float):
-    """P_l(s) F_j(s) at s = s_t + h for the body's own target (s_t, theta_t)."""
+    """P_l(s) [F^D_j(s) + |J_lj| F^S_j(s)] at s = s_t + h for the body's own
+    target (s_t, theta_t); ``pan_jac`` is |J| at the panel's nodes (order, n_theta)."""
     geom = bn.geom
     s = s_t + h
     r, dr, rt, c, alpha = geom.self_ring(s_t, theta_t, h)
     N = bn.n_theta // 2
-    G, Gr, Gz = modal_coeffs(r, rt, c, k, N, dr=dr)
-    W0 = lagrange_weights(G, alpha, bn.n_theta)
-    Wr = lagrange_weights(Gr, alpha, bn.n_theta)
-    Wz = lagrange_weights(Gz, alpha, bn.n_theta)
-    nr, nz, _ = geom.normal_parts(np.full(bn.n_theta, s), bn.theta)
-    F = nr * Wr + nz * Wz - 1j * eta * W0
+    G, Gr, Gz = modal_coeffs(r, rt, c, k, N + 1, dr=dr)
+    W0 = lagrange_weights(G[: N + 1], alpha, bn.n_theta)
+    Wr = lagrange_weights(Gr[: N + 1], alpha, bn.n_theta)
+    Wrc = lagrange_weights_cos_theta(Gr, alpha, bn.n_theta)
+    Wz = lagrange_weights(Gz[: N + 1], alpha, bn.n_theta)
+    g = {kk: float(np.asarray(v).reshape(-1)[0]) for kk, v in geom.ring(np.array([s])).items()
+         if kk in ("r", "dr", "dl")}
+    FD = g["r"] * g["dl"] * (Wr - geom.kappa * g["r"] * Wrc) - g["r"] * g["dr"] * Wz
+    FS = -1j * eta * W0
     P = lagrange_basis(pan_nodes, s)
-    return P[:, None] * F[None, :]
+    return P[:, None] * (FD[None, :] + pan_jac * FS[None, :])
 
 
 def _adaptive(fun, tol_rel: float, max_intervals: int = 500):
@@ -157,6 +169,7 @@ def self_block_rows(bn: BodyNodes, rows, k: float, eta: float, tol: float = 1e-1
                 continue
             lo, hi = bn.breaks[i], bn.breaks[i + 1]
             pan_nodes = bn.s[i * order:(i + 1) * order]
+            pan_jac = bn.jac[cols].reshape(order, nth)
             pieces = []
             if i == p:
                 pieces = [(s_t, lo), (s_t, hi)]
@@ -171,10 +184,10 @@ def self_block_rows(bn: BodyNodes, rows, k: float, eta: float, tol: float = 1e-1
 
                 def fun(v, h0=h0, L=L):
                     h = h0 + L * v ** 4
-                    return _integrand(bn, s_t, theta_t, h, pan_nodes, k, eta) * (4 * abs(L) * v ** 3)
+                    return _integrand(bn, s_t, theta_t, h, pan_nodes, pan_jac, k, eta) * (4 * abs(L) * v ** 3)
 
                 acc += _adaptive(fun, tol)
-            out[ri, cols] = acc.reshape(-1) * bn.jac[cols]
+            out[ri, cols] = acc.reshape(-1)
         out[ri, t] += 0.5
     return out
 

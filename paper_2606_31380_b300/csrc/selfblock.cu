@@ -1,6 +1,11 @@
 // Self-block assembly (Sec. 3.1-3.4): one row of the combined-layer self block
-//   A_b[t, (i,l,j)] = 1/2 delta + |J_ilj| int_{panel i} P_l(s) F_j(s) ds,
-//   F_j(s) = n_r(s,theta_j) W^r_j(s) + n_z(s,theta_j) W^z_j(s) - i eta W^0_j(s),
+//   A_b[t, (i,l,j)] = 1/2 delta + int_{panel i} P_l(s) [F^D_j(s) + |J_ilj| F^S_j(s)] ds,
+//   F^D_j = int [(|J| n_r) K^r + (|J| n_z) K^z] L_j dtheta,  F^S_j = -i eta int G L_j dtheta,
+// where the double layer integrates the exact area-weighted normal
+// |J| n_r = r l'(1 - kappa r cos theta), |J| n_z = -r r' against an
+// interpolant of mu (its cos(theta) factor shifts the modal coefficients),
+// and the single layer keeps the interpolant of mu |J| (the paper's); on
+// bodies of revolution the two readings coincide.
 // per CTA, for every panel i within one of the target's panel (Eq. sx);
 // farther panels take the plain smooth rule.  W_j = int K L_j dtheta comes
 // from the modal Green's functions (Eq. modalgreen) of the source ring at s:
@@ -14,8 +19,10 @@
 //                cosine DFT (all kernels are even in phi = theta - alpha).
 // The outer s-integral replaces the paper's generalised Gaussian tables
 // (not available) with a composite rule: dyadic sub-panels toward the
-// (near-)singular point with order+4 Gauss-Legendre nodes each, and a
-// graded innermost panel (u^6 substitution, 20 nodes) for the logarithm.
+// (near-)singular point with order+4 Gauss-Legendre nodes each (2 order + 4
+// on the outermost one, where the Lagrange basis P_l varies fastest next to
+// the panel end), and a graded innermost panel (u^6 substitution, 20 nodes)
+// for the logarithm.
 // Ring-target geometry uses difference formulas in h = s - s_t so that
 // r - r~ and c keep full relative precision as h -> 0 (the double-layer
 // pieces W^r, W^z each grow like 1/|h| and cancel in F).
@@ -28,12 +35,12 @@ namespace {
 
 constexpr int NT = 128;      // threads per CTA
 constexpr int BATCH = 16;    // outer nodes whose recursions run together (warp 0)
-constexpr int MAXQ = 1024;   // outer nodes per row
+constexpr int MAXQ = 1152;   // outer nodes per row
 constexpr int MAXP = 96;     // highest static mode N + n1 + 1
 constexpr int MAXM2 = 96;    // M/2 + 1 samples of the smooth factors
 constexpr int MAXN1 = 88;    // highest smooth-factor mode + 2
 constexpr int MAXN = 32;     // N = n_theta / 2
-constexpr int MAXORD = 19;   // keeps 40 (order + 4) + 72 outer nodes <= MAXQ
+constexpr int MAXORD = 19;
 
 struct RowShared {
   // outer nodes of the row
@@ -49,10 +56,9 @@ struct RowShared {
   double fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho)
   double fc[3][MAXN1 + 1];      // their cosine coefficients
   double hr[MAXN1 + 1], hz[MAXN1 + 1], pr[MAXN1 + 1], pz[MAXN1 + 1], f2[MAXN1 + 1];
-  double gre[3][MAXN + 1], gim[3][MAXN + 1];  // G^, d_r G^, d_z G^ (phi coefficients)
+  double gre[3][MAXN + 2], gim[3][MAXN + 2];  // G^, d_r G^, d_z G^ (phi coefficients, m <= N+1)
   double cma[MAXN + 1], sma[MAXN + 1];
-  double wre[3][2 * MAXN], wim[3][2 * MAXN];
-  double nr[2 * MAXN], nz[2 * MAXN];
+  double wre[5][2 * MAXN], wim[5][2 * MAXN];  // W^0, W^r, W^z, W^r cos-even, W^r sin-odd
   double pl[MAXORD];
   // row constants
   double s2tab[MAXM2];     // sin^2(pi q / M)
@@ -259,7 +265,9 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   const double* gl_x = rules + B.rule;              // [order] on [-1,1]
   const double* dy_x = gl_x + 2 * order;            // [order+4] on [0,1]
   const double* dy_w = dy_x + (order + 4);
-  const double* in_x = dy_w + (order + 4);          // [20]
+  const double* d0_x = dy_w + (order + 4);          // [2 order+4] on [0,1], outermost level
+  const double* d0_w = d0_x + (2 * order + 4);
+  const double* in_x = d0_w + (2 * order + 4);      // [20]
   const double* in_w = in_x + 20;
   const double* ad_x = in_w + 20;                   // [16]
   const double* ad_w = ad_x + 16;
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   const bool kz = (k == 0.0);
   const int n1 = kz ? 0 : B.n1;
   const int M = B.M, M2 = M / 2;
-  const int P = N + n1 + 1;
+  const int P = N + n1 + 2;
 
   for (int e = tid; e < nbn; e += NT) acc[e] = make_double2(0.0, 0.0);
   // outer nodes (thread 0 builds the list; pieces follow the panel layout)
@@ -295,10 +303,13 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         double top = 1.0;
         for (int kk = 0; kk < K; ++kk) {
           const double bot = 0.5 * top;
-          for (int gq = 0; gq < ng && nq < MAXQ; ++gq, ++nq) {
-            const double v = bot + (top - bot) * dy_x[gq];
+          const int nk = kk == 0 ? ng + order : ng;
+          const double* kx = kk == 0 ? d0_x : dy_x;
+          const double* kw = kk == 0 ? d0_w : dy_w;
+          for (int gq = 0; gq < nk && nq < MAXQ; ++gq, ++nq) {
+            const double v = bot + (top - bot) * kx[gq];
             S.qh[nq] = h0 + L * v;
-            S.qw[nq] = (top - bot) * dy_w[gq] * aL;
+            S.qw[nq] = (top - bot) * kw[gq] * aL;
             S.qp[nq] = i;
           }
           top = bot;
@@ -378,9 +389,9 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         }
         __syncthreads();
       }
-      // D: modal coefficients of G, d_r G, d_z G for m = 0..N
-      for (int e = tid; e < 3 * (N + 1); e += NT) {
-        const int comp = e / (N + 1), m = e % (N + 1);
+      // D: modal coefficients of G, d_r G, d_z G for m = 0..N+1
+      for (int e = tid; e < 3 * (N + 2); e += NT) {
+        const int comp = e / (N + 2), m = e % (N + 2);
         double re, im = 0.0;
         if (kz) {
           const double g0 = q[m] * scale;
@@ -405,14 +416,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         S.gre[comp][m] = re;
         S.gim[comp][m] = im;
       }
-      // E (part): normal components at (s, theta_j) and Lagrange basis P_l(s)
-      for (int j = tid; j < nth; j += NT) {
-        const double A = sc[9] * (1.0 - sc[11] * S.cth[j]);
-        const double Bv = sc[10];
-        const double hh = rsqrt(A * A + Bv * Bv);
-        S.nr[j] = A * hh;
-        S.nz[j] = -Bv * hh;
-      }
+      // E (part): Lagrange basis P_l(s)
       const int ip = S.qp[b0 + bi];
       if (tid < order) {
         const double xs = (s - (-M_PI / 2 + pw * ip)) / pw * 2.0 - 1.0;  // panel coordinate
@@ -423,29 +427,60 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       }
       __syncthreads();
       // E: W_j = (1/2N)[G_0 + 2 sum_{m<N} G_m cos m(theta_j - alpha) + G_N cos N(theta_j - alpha)]
-      for (int e = tid; e < 3 * nth; e += NT) {
+      // for G, d_r G, d_z G, and for d_r G cos(phi) (coefficients (g_{m-1}+g_{m+1})/2);
+      // the odd part d_r G sin(phi) (coefficients (g_{m-1}-g_{m+1})/2i) gives
+      // (1/2N) sum_{m=1}^{N} f_m (g_{m-1} - g_{m+1}) sin m(theta_j - alpha), f_N = 1/2.
+      for (int e = tid; e < 5 * nth; e += NT) {
         const int comp = e / nth, j = e % nth;
-        double sre = S.gre[comp][0], sim = S.gim[comp][0];
+        const int src = comp < 3 ? comp : 1;
+        const double* gr = S.gre[src];
+        const double* gi = S.gim[src];
+        double sre, sim;
+        if (comp == 3) {
+          sre = gr[1];
+          sim = gi[1];
+        } else if (comp == 4) {
+          sre = sim = 0.0;
+        } else {
+          sre = gr[0];
+          sim = gi[0];
+        }
         int idx = 0;
         for (int m = 1; m <= N; ++m) {
           idx += j;
           if (idx >= nth) idx -= nth;
-          const double cm = S.cth[idx] * S.cma[m] + S.sth[idx] * S.sma[m];
-          const double f = (m < N) ? 2.0 * cm : cm;
-          sre += f * S.gre[comp][m];
-          sim += f * S.gim[comp][m];
+          double cr, ci, f;
+          if (comp == 4) {
+            const double sm = S.sth[idx] * S.cma[m] - S.cth[idx] * S.sma[m];  // sin m(theta_j - alpha)
+            f = (m < N ? 1.0 : 0.5) * sm;
+            cr = gr[m - 1] - gr[m + 1];
+            ci = gi[m - 1] - gi[m + 1];
+          } else {
+            const double cm = S.cth[idx] * S.cma[m] + S.sth[idx] * S.sma[m];  // cos m(theta_j - alpha)
+            f = (m < N) ? 2.0 * cm : cm;
+            cr = comp == 3 ? 0.5 * (gr[m - 1] + gr[m + 1]) : gr[m];
+            ci = comp == 3 ? 0.5 * (gi[m - 1] + gi[m + 1]) : gi[m];
+          }
+          sre += f * cr;
+          sim += f * ci;
         }
         S.wre[comp][j] = sre / nth;
         S.wim[comp][j] = sim / nth;
       }
       __syncthreads();
-      // F: accumulate w * P_l(s) * F_j
+      // F: accumulate w P_l(s) [F^D_j + |J_lj| F^S_j]
       const double wq = S.qw[b0 + bi];
       const int base = ip * per_panel;
+      const double rl = r * sc[9], kr = sc[11], rrp = r * sc[10];
+      double sal, cal;
+      sincos(alpha, &sal, &cal);
       for (int e = tid; e < per_panel; e += NT) {
         const int l = e / nth, j = e % nth;
-        const double fre = S.nr[j] * S.wre[1][j] + S.nz[j] * S.wre[2][j] + eta * S.wim[0][j];
-        const double fim = S.nr[j] * S.wim[1][j] + S.nz[j] * S.wim[2][j] - eta * S.wre[0][j];
+        const double J = jac[B.offset + base + e];
+        const double rcre = cal * S.wre[3][j] - sal * S.wre[4][j];  // int d_r G cos(theta) L_j
+        const double rcim = cal * S.wim[3][j] - sal * S.wim[4][j];
+        const double fre = rl * (S.wre[1][j] - kr * rcre) - rrp * S.wre[2][j] + J * eta * S.wim[0][j];
+        const double fim = rl * (S.wim[1][j] - kr * rcim) - rrp * S.wim[2][j] - J * eta * S.wre[0][j];
         const double f = wq * S.pl[l];
         acc[base + e].x += f * fre;
         acc[base + e].y += f * fim;
@@ -461,8 +496,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
     const long long src = B.offset + e;
     double2 v;
     if (abs(i - p) <= 1) {
-      const double J = jac[src];
-      v = make_double2(acc[e].x * J, acc[e].y * J);
+      v = acc[e];
     } else {
       double kre, kim;
       smooth_kernel(xt, x64[src], n64[src], k, eta, &kre, &kim);
@@ -489,7 +523,9 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   for (int b = 0; b < nb; ++b) {
     const BodyHost& bh = c->bodies[b];
     const qams_body_desc& d = bh.d;
-    if (d.order > MAXORD || d.n_theta / 2 > MAXN || 40 * (d.order + 4) + 72 > MAXQ) return QAMS_EINVAL;
+    // outer nodes per row: self panel 2 x (13 (o+4) + (2o+4) + 20), two neighbours 2 x (5 (o+4) + (2o+4) + 16)
+    const int o4 = d.order + 4, maxq = 2 * (13 * o4 + 2 * d.order + 4 + 20) + 2 * (5 * o4 + 2 * d.order + 4 + 16);
+    if (d.order > MAXORD || d.n_theta / 2 > MAXN || maxq > MAXQ) return QAMS_EINVAL;
     if (rule_off[d.order] < 0) {
       rule_off[d.order] = (int)rules.size();
       std::vector<double> x, w;
@@ -497,6 +533,11 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
       rules.insert(rules.end(), x.begin(), x.end());
       rules.insert(rules.end(), w.begin(), w.end());
       qams_gauss_legendre(d.order + 4, x, w);
+      for (auto& v : x) v = 0.5 * (v + 1.0);
+      for (auto& v : w) v *= 0.5;
+      rules.insert(rules.end(), x.begin(), x.end());
+      rules.insert(rules.end(), w.begin(), w.end());
+      qams_gauss_legendre(2 * d.order + 4, x, w);
       for (auto& v : x) v = 0.5 * (v + 1.0);
       for (auto& v : w) v *= 0.5;
       rules.insert(rules.end(), x.begin(), x.end());
@@ -532,7 +573,7 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
     const double rmax = d.base_radius * (1.0 + amp);
     A.n1 = (int)std::ceil(1.3 * c->k * rmax + 16.0);
     A.M = 2 * (A.n1 + 8);
-    if (A.n1 + 2 > MAXN1 || A.M / 2 + 1 > MAXM2 || d.n_theta / 2 + A.n1 + 1 > MAXP || 2 * A.M > 4 * MAXM2)
+    if (A.n1 + 2 > MAXN1 || A.M / 2 + 1 > MAXM2 || d.n_theta / 2 + A.n1 + 2 > MAXP || 2 * A.M > 4 * MAXM2)
       return QAMS_EINVAL;
     A.rule = rule_off[d.order];
     max_nb = std::max(max_nb, bh.n);

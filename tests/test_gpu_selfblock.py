@@ -63,13 +63,12 @@ def test_curved_body_rows_match_oracle(k, eta, disc):
 
 
 def test_gauss_identity_on_gpu_block():
-    # k -> 0, eta = 0: (1/2 I + D) 1 = 0 up to discretisation error, refining converges
-    errs = []
+    """k -> 0, eta = 0: (1/2 I + D) 1 = 0 (Gauss's lemma) holds to quadrature
+    accuracy on every row, for several discretisations."""
     for disc in [(1, 8, 16), (2, 12, 24), (2, 16, 32)]:
         body = scenes.Body(*disc, **CURVED)
         _, A = gpu_block(scenes.Scene("g", [body], 1e-9, 0.0, scenes.paper_direction()))
-        errs.append(np.max(np.abs(A.sum(axis=1))))
-    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-6
+        assert np.max(np.abs(A.sum(axis=1))) < 1e-11
 
 
 def test_apply_matches_oracle_congruent_bodies():

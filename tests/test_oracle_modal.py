@@ -82,3 +82,24 @@ def test_lagrange_weights_exact_for_trig_polynomials():
         L = (1 + 2 * sum(np.cos(m * (th - tj)) for m in range(1, N)) + np.cos(N * (th - tj))) / (2 * N)
         ref.append(np.sum(G * L) * 2 * np.pi / M)
     assert np.max(np.abs(W - np.array(ref))) < 1e-14
+
+
+def test_cos_theta_weights_against_trapezoid():
+    """int K^r(theta - alpha) cos(theta) L_j dtheta from shifted modal coefficients
+    (the area-weighted normal's cos(theta) factor) against a fine trapezoid."""
+    from oracle.modal import lagrange_weights_cos_theta
+    r, rt, c, k, N, al = 0.4, 0.5, 0.3, 3.0, 8, 0.7
+    G, Gr, Gz = modal_coeffs(r, rt, c, k, N + 1)
+    W = lagrange_weights_cos_theta(Gr, al, 2 * N)
+    M = 1 << 13
+    th = 2 * np.pi * np.arange(M) / M
+    phi = th - al
+    rho = np.sqrt(rt ** 2 + r ** 2 + c ** 2 - 2 * r * rt * np.cos(phi))
+    dG = np.exp(1j * k * rho) * (1j * k * rho - 1) / (4 * np.pi * rho ** 2)
+    Kr = dG * (r - rt * np.cos(phi)) / rho
+    ref = []
+    for j in range(2 * N):
+        tj = j * np.pi / N
+        L = (1 + 2 * sum(np.cos(m * (th - tj)) for m in range(1, N)) + np.cos(N * (th - tj))) / (2 * N)
+        ref.append(np.sum(Kr * np.cos(th) * L) * 2 * np.pi / M)
+    assert np.max(np.abs(W - np.array(ref))) < 1e-14 * np.max(np.abs(ref))

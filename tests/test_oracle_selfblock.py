@@ -14,16 +14,16 @@ from oracle.selfblock import self_block, self_block_rows
 CURVED = dict(base_radius=0.5, mode_cos=(0.06, 0.03), mode_sin=(0.04,), axis_length=1.0, curvature=0.35)
 
 
-def test_gauss_identity_converges_on_curved_body():
-    # k = 0, eta = 0: (1/2 I + D) 1 = 0 on a closed surface (Gauss's lemma)
-    errs = []
+def test_gauss_identity_on_curved_body():
+    """k = 0, eta = 0: (1/2 I + D) 1 = 0 on a closed surface (Gauss's lemma).
+    The double layer integrates the exact area-weighted normal against an
+    interpolant of mu, which is exact for mu = 1, so the identity holds to
+    the accuracy of the quadrature itself at any discretisation."""
     for disc in [(1, 8, 16), (2, 12, 24)]:
         bn = body_nodes(scenes.Body(*disc, **CURVED))
-        rows = [bn.count // 2 + 3, 5]
+        rows = [bn.count // 2 + 3, 5, bn.count - 1]
         A = self_block_rows(bn, rows, 0.0, 0.0, tol=1e-13)
-        errs.append(np.max(np.abs(A.sum(axis=1))))
-    # rows next to a pole converge slowest (the paper refines there dyadically)
-    assert errs[1] < 2e-5 and errs[0] / errs[1] > 100
+        assert np.max(np.abs(A.sum(axis=1))) < 1e-12
 
 
 def test_sphere_eigenvalues():

@@ -46,7 +46,8 @@ enum {
   QAMS_ENUMERIC = -5,   /* NaN/Inf in a residual                          */
   QAMS_ETIMEOUT = -6,   /* a bounded device wait gave up                  */
   QAMS_ECANCELLED = -7, /* cancelled between restart cycles               */
-  QAMS_ECUDA = -8       /* a CUDA runtime call failed                     */
+  QAMS_ECUDA = -8,      /* a CUDA runtime call failed                     */
+  QAMS_ESCRATCH = -9    /* problem too large for the static scratch       */
 };
 
 enum { QAMS_PREC_FP64 = 0, QAMS_PREC_FP32 = 1 };
@@ -178,6 +179,36 @@ void qams_solve_opts_default(qams_solve_opts* opts);
  * filled), QAMS_ENUMERIC, QAMS_EBUDGET, QAMS_ECUDA. */
 int qams_solve(qams_ctx* ctx, int R, const void* rhs_dev, void* mu_dev, const qams_solve_opts* opts,
                qams_solve_stats* stats, void* stream);
+
+/* The FP32 inter-body pair sum of qams_pairsum, for callers that cannot
+ * allocate device memory: a host framework that reserves all device memory
+ * for its own pool up front, or a latency-critical loop that cannot take
+ * cudaMalloc's implicit device synchronisation.  It needs no context and
+ * allocates nothing: every input and output is a caller-owned buffer, and
+ * the call's scratch (launch tables and per-split partial sums) lives in a
+ * 32 MiB array of static device memory that every GPU loading the library
+ * holds until the process exits.  The paper has no counterpart; this is an
+ * interface addition.
+ *   body_offsets_host [n_bodies+1]: first node of each body, [0] = 0,
+ *                     [n_bodies] = N, strictly increasing (host memory);
+ *   centers_host      [n_bodies][3]: body centres c_b (FP64, host memory);
+ *   x32_dev           float4 [N]: node position minus its body's centre
+ *                     (x, y, z) and quadrature weight w in .w;
+ *   n32_dev           float4 [N]: unit normal (x, y, z), .w unused;
+ *   sigma_dev, y_dev  complex64 [N][R], y overwritten (as in qams_pairsum).
+ * Works on the current CUDA device.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls on a device share the one array:
+ * calls that overlap on the GPU race (serialise them on one stream).
+ * Nothing in the array needs to start at zero.  Blocking (returns after its
+ * work on `stream` finished).
+ * When the per-split partial sums would not fit in the array, fewer source
+ * splits are used (down to one, which needs no partial sums).
+ * Errors: QAMS_EINVAL, QAMS_ESCRATCH (more than 4096 bodies or more than
+ * 65536 target tiles of 128 nodes), QAMS_ECUDA. */
+int qams_pairsum_f32_static(int n_bodies, const long long* body_offsets_host, const double* centers_host,
+                            const void* x32_dev, const void* n32_dev, int R, const void* sigma_dev, void* y_dev,
+                            double k, double eta, void* stream);
 
 /* Right-hand sides b = -u^inc = -e^{ik d.x} (Sec. 6) for R unit directions
  * dirs_host [R][3]; rhs_dev is [N][R] complex128. */

@@ -65,6 +65,7 @@ def load_library():
         "qams_copy_selfblock": (i, [vp, i, vp, vp]),
         "qams_apply": (i, [vp, i, vp, vp, i, vp]),
         "qams_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
+        "qams_pairsum_f32_static": (i, [i, vp, vp, vp, vp, i, vp, vp, d, d, vp]),
         "qams_solve": (i, [vp, i, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveStats), vp]),
         "qams_farfield": (i, [vp, i, vp, i, vp, vp, vp]),
     }

@@ -56,6 +56,7 @@ const char* qams_strerror(int code) {
     case QAMS_ETIMEOUT: return "bounded device wait timed out";
     case QAMS_ECANCELLED: return "cancelled";
     case QAMS_ECUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
+    case QAMS_ESCRATCH: return "problem exceeds the static scratch of the no-allocation entry point";
     default: return "unknown error";
   }
 }

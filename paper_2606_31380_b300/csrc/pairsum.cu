@@ -328,3 +328,141 @@ int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int prec
   }
   return QAMS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Pair sum without device allocation.
+//
+// For callers that cannot call cudaMalloc -- for example a host framework
+// that reserves all device memory for its own pool up front, or a
+// latency-critical loop that cannot afford cudaMalloc's implicit device
+// synchronisation -- this variant takes every input and output from the
+// caller and keeps its own scratch (launch tables and the per-split partial
+// sums) in the file-scope array below, which every GPU that loads the
+// library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t STATIC_SCRATCH_BYTES = 32u << 20;  // 32 MiB
+constexpr int STATIC_MAX_BODIES = 4096;
+constexpr int STATIC_MAX_TILES = 65536;
+constexpr int STATIC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+// Device address of g_static_scratch per device (host code cannot use the
+// symbol's name as a device pointer); filled on the first call on a device.
+static void* g_static_ptr[STATIC_MAX_DEVICES];
+
+}  // namespace
+
+extern "C" int qams_pairsum_f32_static(int n_bodies, const long long* body_offsets_host, const double* centers_host,
+                                       const void* x32_dev, const void* n32_dev, int R, const void* sigma_dev,
+                                       void* y_dev, double k, double eta, void* stream) {
+  if (n_bodies < 1 || !body_offsets_host || !centers_host || !x32_dev || !n32_dev || R < 1 || !sigma_dev ||
+      !y_dev || !(k > 0) || !std::isfinite(k) || !std::isfinite(eta))
+    return QAMS_EINVAL;
+  if (n_bodies > STATIC_MAX_BODIES) return QAMS_ESCRATCH;
+  const long long N = body_offsets_host[n_bodies];
+  if (body_offsets_host[0] != 0 || N < 1) return QAMS_EINVAL;
+  for (int b = 0; b < n_bodies; ++b)
+    if (body_offsets_host[b + 1] <= body_offsets_host[b]) return QAMS_EINVAL;
+  int dev = 0;
+  QAMS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= STATIC_MAX_DEVICES) return QAMS_ESCRATCH;
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    QAMS_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_ptr[dev] = p;
+  }
+  unsigned char* base = (unsigned char*)g_static_ptr[dev];
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // launch tables, built like qams_pairsum_prepare's (host memory only)
+  std::vector<TargetTile> tiles;
+  for (int b = 0; b < n_bodies; ++b) {
+    const long long o = body_offsets_host[b], n = body_offsets_host[b + 1] - o;
+    for (long long s = 0; s < n; s += TILE) tiles.push_back({b, (int)std::min<long long>(TILE, n - s), o + s});
+  }
+  if ((long long)tiles.size() > STATIC_MAX_TILES) return QAMS_ESCRATCH;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    const size_t at = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return base + at;
+  };
+  long long* d_boff = (long long*)carve(sizeof(long long) * (n_bodies + 1));
+  qd4* d_cent = (qd4*)carve(sizeof(qd4) * n_bodies);
+  TargetTile* d_tiles = (TargetTile*)carve(sizeof(TargetTile) * tiles.size());
+  SourceSplit* d_splits = (SourceSplit*)carve(sizeof(SourceSplit) * n_bodies);
+  const size_t fixed = off;
+  if (fixed >= STATIC_SCRATCH_BYTES) return QAMS_ESCRATCH;
+  const size_t room = STATIC_SCRATCH_BYTES - fixed;
+
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int rc_max = pick_rc(R);
+  long long want = std::max(1LL, std::min<long long>(n_bodies, (8LL * sms + (long long)tiles.size() - 1) /
+                                                                   (long long)tiles.size()));
+  // partial sums must fit in the remaining scratch
+  const long long fit = (long long)(room / (sizeof(float2) * (size_t)N * rc_max));
+  const int S = (int)std::max(1LL, std::min(want, fit));
+  std::vector<SourceSplit> splits;
+  const long long per = (N + S - 1) / S;
+  long long acc = 0;
+  int begin = 0;
+  for (int b = 0; b < n_bodies; ++b) {
+    acc += body_offsets_host[b + 1] - body_offsets_host[b];
+    if (acc >= per * ((long long)splits.size() + 1) || b == n_bodies - 1) {
+      splits.push_back({begin, b + 1});
+      begin = b + 1;
+    }
+  }
+  const int Sr = (int)splits.size();
+  float2* d_part = (float2*)carve(0);
+  std::vector<qd4> cent(n_bodies);
+  for (int b = 0; b < n_bodies; ++b) {
+    cent[b].x = centers_host[3 * b];
+    cent[b].y = centers_host[3 * b + 1];
+    cent[b].z = centers_host[3 * b + 2];
+    cent[b].w = 0.0;
+  }
+  // every table entry and every partial sum is written before it is read,
+  // so nothing left in the array by an earlier call needs clearing
+  QAMS_CUDA(cudaMemcpyAsync(d_boff, body_offsets_host, sizeof(long long) * (n_bodies + 1), cudaMemcpyHostToDevice, st));
+  QAMS_CUDA(cudaMemcpyAsync(d_cent, cent.data(), sizeof(qd4) * n_bodies, cudaMemcpyHostToDevice, st));
+  QAMS_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TargetTile) * tiles.size(), cudaMemcpyHostToDevice, st));
+  QAMS_CUDA(cudaMemcpyAsync(d_splits, splits.data(), sizeof(SourceSplit) * Sr, cudaMemcpyHostToDevice, st));
+
+  dim3 grid((unsigned)tiles.size(), (unsigned)Sr);
+  for (int r0 = 0; r0 < R;) {
+    const int rcur = pick_rc(R - r0);
+    float2* out = Sr > 1 ? d_part : (float2*)y_dev;
+    const long long stride = Sr > 1 ? N * rcur : 0;
+    const int ld = Sr > 1 ? rcur : R, or0 = Sr > 1 ? 0 : r0;
+    const float2* sg = (const float2*)sigma_dev;
+#define QAMS_STATIC_LAUNCH(RCV)                                                                                  \
+  pairsum_f32_kernel<RCV><<<grid, TILE, 0, st>>>(d_tiles, d_splits, d_boff, d_cent, (const float4*)x32_dev,    \
+                                                 (const float4*)n32_dev, sg, R, r0, k, eta, out, stride, ld, or0)
+    switch (rcur) {
+      case 16: QAMS_STATIC_LAUNCH(16); break;
+      case 8: QAMS_STATIC_LAUNCH(8); break;
+      case 4: QAMS_STATIC_LAUNCH(4); break;
+      case 2: QAMS_STATIC_LAUNCH(2); break;
+      default: QAMS_STATIC_LAUNCH(1); break;
+    }
+#undef QAMS_STATIC_LAUNCH
+    qams_count_launch();
+    QAMS_CUDA(cudaGetLastError());
+    if (Sr > 1) {
+      const long long n = N * rcur;
+      reduce_splits_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_part, Sr, N, rcur, (float2*)y_dev,
+                                                                                R, r0);
+      qams_count_launch();
+      QAMS_CUDA(cudaGetLastError());
+    }
+    r0 += rcur;
+  }
+  // the host tables above are read by the copies: finish them before returning
+  QAMS_CUDA(cudaStreamSynchronize(st));
+  return QAMS_OK;
+}

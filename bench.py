@@ -124,9 +124,10 @@ def fp64_peak_tflops(torch):
 
 def assembly_flops(scene):
     """Algorithmic FP64 operations of one self-block assembly, counted from the
-    kernel's dense loops per outer quadrature node (cosine transforms,
-    convolutions, Lagrange weights, accumulation); transcendental calls and
-    the Q recursions are not counted, so this undercounts the work."""
+    kernel's dense loops: per outer quadrature node the cosine transforms,
+    convolutions, theta-coefficients and accumulation, per row and near panel
+    the inverse DFT; transcendental calls and the Q recursions are not
+    counted, so this undercounts the work."""
     import numpy as np
     total = 0.0
     for b in scene.bodies:
@@ -135,9 +136,11 @@ def assembly_flops(scene):
         amp = sum(abs(x) for x in b.mode_cos) + sum(abs(x) for x in b.mode_sin)
         n1 = math.ceil(1.3 * scene.k * b.base_radius * (1 + amp) + 16.0)
         M2 = n1 + 8
-        # cosine DFTs (3 factors), convolutions (3 kernels, modes 0..N+1),
-        # Lagrange weights (5 sums of N terms per azimuth), accumulation
-        per_node = (2 * 3 * (n1 + 2) * (M2 - 1) + 15 * (N + 2) * (2 * n1 + 1) + 5 * 7 * nth * N + 20 * order * nth)
+        # per outer node: cosine DFTs of 3 smooth factors, convolutions (3 kernels,
+        # modes 0..N+1), theta-coefficients of the two integrands, accumulation
+        per_node = 6 * (n1 + 2) * (M2 - 1) + 10 * (N + 2) * (2 * n1 + 1) + 40 * nth + 8 * order * nth
+        # per row and near panel: inverse DFT of the accumulated coefficients
+        per_panel_flush = 8 * order * nth * nth
         x, _ = np.polynomial.legendre.leggauss(order)
         pw = math.pi / npan
         nodes_per_row = 0
@@ -146,16 +149,19 @@ def assembly_flops(scene):
                 s_t = -math.pi / 2 + pw * (p + 0.5 + 0.5 * x[l])
                 dpole = min(s_t + math.pi / 2, math.pi / 2 - s_t)
                 cnt = 0
+                near = 0
                 for i in range(max(0, p - 1), min(npan - 1, p + 1) + 1):
+                    near += 1
                     lo, hi = -math.pi / 2 + pw * i, -math.pi / 2 + pw * (i + 1)
+                    levels = lambda K: (2 * order + 4) + (order + 4 if K > 1 else 0) + 12 * max(0, K - 2)
                     if i == p:
                         for L in (abs(lo - s_t), abs(hi - s_t)):
                             K = min(14, max(5, math.ceil(math.log2(L / (0.5 * dpole)))))
-                            cnt += K * (order + 4) + order + 20
+                            cnt += levels(K) + 20
                     else:
-                        cnt += 6 * (order + 4) + order + 16
-                nodes_per_row += cnt * nth
-        total += nodes_per_row * per_node
+                        cnt += levels(6) + 16
+                nodes_per_row += cnt * nth * per_node + near * nth * per_panel_flush
+        total += nodes_per_row
     return total
 
 
@@ -172,6 +178,10 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     sc = scenes.config(args.config, request_id=rank)  # replicas: independent request per rank
+    if args.bodies:
+        # a smaller case of the same workload (profiling captures)
+        sc = scenes.Scene(sc.name + f" (first {args.bodies} bodies)", sc.bodies[:args.bodies], sc.k, sc.eta,
+                          sc.directions)
     R = sc.n_rhs
     xh = far_directions()
     M = xh.shape[0]
@@ -395,6 +405,7 @@ def main():
     ap.add_argument("--config", type=int, default=1, help="workload index (1 = 16 bodies x 2048 nodes, k = 5)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bodies", type=int, default=0, help="use only the first B bodies (small profiling case)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))

@@ -1,14 +1,14 @@
-// Self-block assembly (Sec. 3.1-3.4): one row of the combined-layer self block
+// Self-block assembly (Sec. 3.1-3.4): one row of the combined-layer self block per CTA,
 //   A_b[t, (i,l,j)] = 1/2 delta + int_{panel i} P_l(s) [F^D_j(s) + |J_ilj| F^S_j(s)] ds,
 //   F^D_j = int [(|J| n_r) K^r + (|J| n_z) K^z] L_j dtheta,  F^S_j = -i eta int G L_j dtheta,
-// where the double layer integrates the exact area-weighted normal
-// |J| n_r = r l'(1 - kappa r cos theta), |J| n_z = -r r' against an
-// interpolant of mu (its cos(theta) factor shifts the modal coefficients),
-// and the single layer keeps the interpolant of mu |J| (the paper's); on
-// bodies of revolution the two readings coincide.
-// per CTA, for every panel i within one of the target's panel (Eq. sx);
-// farther panels take the plain smooth rule.  W_j = int K L_j dtheta comes
-// from the modal Green's functions (Eq. modalgreen) of the source ring at s:
+// for every panel i within one of the target's panel (Eq. sx); farther panels
+// take the plain smooth rule.  The double layer integrates the exact
+// area-weighted normal |J| n_r = r l'(1 - kappa r cos theta), |J| n_z = -r r'
+// against an interpolant of mu; the single layer keeps the interpolant of
+// mu |J| (the paper's); on bodies of revolution the two coincide.
+//
+// Azimuthal integrals come from the modal Green's functions (Eq. modalgreen)
+// of the source ring at s:
 //   static part  g^_m = Q_{m-1/2}(chi)/(2 pi sqrt(r r~)) (Eq. modal0), Q by the
 //                recursion of Eq. leg_recur (forward near chi = 1, Miller's
 //                backward recursion on ratios otherwise), Q' by Eq. dleg_recur;
@@ -17,15 +17,19 @@
 //                factors cos(k rho), sinc(k rho) and
 //                (k rho cos k rho - sin k rho)/(k rho)^3 are transformed by a
 //                cosine DFT (all kernels are even in phi = theta - alpha).
-// The outer s-integral replaces the paper's generalised Gaussian tables
-// (not available) with a composite rule: dyadic sub-panels toward the
-// (near-)singular point with order+4 Gauss-Legendre nodes each (2 order + 4
-// on the outermost one, where the Lagrange basis P_l varies fastest next to
-// the panel end), and a graded innermost panel (u^6 substitution, 20 nodes)
-// for the logarithm.
-// Ring-target geometry uses difference formulas in h = s - s_t so that
-// r - r~ and c keep full relative precision as h -> 0 (the double-layer
-// pieces W^r, W^z each grow like 1/|h| and cancel in F).
+// The theta-coefficients of both integrands (k^_|m| e^{-i m alpha}, cos(theta)
+// averaging neighbouring modes) are accumulated over the outer nodes of a
+// panel, weighted by w P_l(s); the inverse DFT against L_j (Sec. 3.1) runs
+// once per panel instead of once per outer node.
+//
+// The outer s-integral replaces the paper's generalised Gaussian tables (not
+// available) with a composite rule: dyadic sub-panels toward the
+// (near-)singular point with 2 order + 4 Gauss-Legendre nodes on the
+// outermost (where P_l varies fastest next to the panel end), order + 4 on
+// the next and 12 on the inner ones, and a graded innermost panel (u^6
+// substitution, 20 nodes) for the logarithm.  Ring-target geometry uses
+// difference formulas in h = s - s_t so that r - r~ and c keep full relative
+// precision as h -> 0 (the double-layer pieces each grow like 1/|h| and cancel).
 #include <algorithm>
 #include <cmath>
 
@@ -42,23 +46,25 @@ constexpr int MAXN1 = 88;    // highest smooth-factor mode + 2
 constexpr int MAXN = 32;     // N = n_theta / 2
 constexpr int MAXORD = 19;
 
-struct RowShared {
+struct alignas(16) RowShared {
   // outer nodes of the row
   double qh[MAXQ];
   double qw[MAXQ];
   int qp[MAXQ];
   int nq;
   // per-batch node data (filled by warp 0)
-  double bq[BATCH][MAXP + 1];   // Q_{m-1/2}, then g^_m
-  double bdq[BATCH][MAXP + 1];  // Q', then d_r g^_m ... see below
+  double bq[BATCH][MAXP + 1];   // Q_{m-1/2}
+  double bdq[BATCH][MAXP + 1];  // dQ_{m-1/2}/dchi
   double bs[BATCH][16];         // scalars
   // per-node work arrays
+  double sg0[MAXP + 1], sgr[MAXP + 1], sgz[MAXP + 1];  // static g^, d_r g^, d_z g^ (modes 0..P)
   double fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho)
   double fc[3][MAXN1 + 1];      // their cosine coefficients
   double hr[MAXN1 + 1], hz[MAXN1 + 1], pr[MAXN1 + 1], pz[MAXN1 + 1], f2[MAXN1 + 1];
   double gre[3][MAXN + 2], gim[3][MAXN + 2];  // G^, d_r G^, d_z G^ (phi coefficients, m <= N+1)
-  double cma[MAXN + 1], sma[MAXN + 1];
-  double wre[5][2 * MAXN], wim[5][2 * MAXN];  // W^0, W^r, W^z, W^r cos-even, W^r sin-odd
+  double cma[MAXN + 2], sma[MAXN + 2];         // cos(m alpha), sin(m alpha)
+  double dre[2 * MAXN], dim_[2 * MAXN];        // theta-coefficients of the double-layer integrand
+  double tre[2 * MAXN], tim[2 * MAXN];         // theta-coefficients of the single-layer integrand
   double pl[MAXORD];
   // row constants
   double s2tab[MAXM2];     // sin^2(pi q / M)
@@ -245,7 +251,10 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
                                                        long long row0, double2* __restrict__ blocks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowShared& S = *reinterpret_cast<RowShared*>(smem_raw);
-  double2* acc = reinterpret_cast<double2*>(smem_raw + sizeof(RowShared));
+  // modal-domain accumulators of the current panel, [order][2N] complex each for the
+  // double layer and the single layer (RowShared is 16-byte aligned, so its size is a
+  // multiple of 16 and these double2 arrays stay aligned)
+  double2* accD = reinterpret_cast<double2*>(smem_raw + sizeof(RowShared));
 
   const long long g = row0 + blockIdx.x;  // global target node
   int lo = 0, hi = nb - 1;
@@ -257,6 +266,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   const int tid = threadIdx.x;
   const int nth = B.n_theta, N = nth / 2, order = B.order;
   const int per_panel = order * nth;
+  double2* accS = accD + per_panel;
   const int nbn = B.n_panels * per_panel;
   const int t = (int)(g - B.offset);
   const int p = t / per_panel;
@@ -271,6 +281,8 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   const double* in_w = in_x + 20;
   const double* ad_x = in_w + 20;                   // [16]
   const double* ad_w = ad_x + 16;
+  const double* g12_x = ad_w + 16;                  // [12], inner dyadic levels
+  const double* g12_w = g12_x + 12;
   const double pw = M_PI / B.n_panels;
   const double s_t = -M_PI / 2 + pw * (p + 0.5 + 0.5 * gl_x[lt]);
   const double th_t = 2.0 * M_PI * jt / nth;
@@ -278,9 +290,10 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   const int n1 = kz ? 0 : B.n1;
   const int M = B.M, M2 = M / 2;
   const int P = N + n1 + 2;
+  double2* row = blocks + B.blk + (long long)t * nbn;
 
-  for (int e = tid; e < nbn; e += NT) acc[e] = make_double2(0.0, 0.0);
-  // outer nodes (thread 0 builds the list; pieces follow the panel layout)
+  for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_double2(0.0, 0.0);
+  // outer nodes (thread 0 builds the list; panels in increasing order, contiguous)
   if (tid == 0) {
     int nq = 0;
     const double dpole = fmin(s_t + M_PI / 2, M_PI / 2 - s_t);
@@ -303,9 +316,9 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         double top = 1.0;
         for (int kk = 0; kk < K; ++kk) {
           const double bot = 0.5 * top;
-          const int nk = kk == 0 ? ng + order : ng;
-          const double* kx = kk == 0 ? d0_x : dy_x;
-          const double* kw = kk == 0 ? d0_w : dy_w;
+          const int nk = kk == 0 ? ng + order : (kk == 1 ? ng : 12);
+          const double* kx = kk == 0 ? d0_x : (kk == 1 ? dy_x : g12_x);
+          const double* kw = kk == 0 ? d0_w : (kk == 1 ? dy_w : g12_w);
           for (int gq = 0; gq < nk && nq < MAXQ; ++gq, ++nq) {
             const double v = bot + (top - bot) * kx[gq];
             S.qh[nq] = h0 + L * v;
@@ -349,7 +362,13 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       const double dchi_r = sc[6], dchi_z = sc[7], s = sc[8];
       const double* q = S.bq[bi];
       const double* dq = S.bdq[bi];
-      // B: samples of the smooth factors, e^{i m alpha}
+      // B: scaled static modal sequences, samples of the smooth factors, cos/sin(m alpha), P_l(s)
+      for (int m = tid; m <= P; m += NT) {
+        const double g0 = q[m] * scale;
+        S.sg0[m] = g0;
+        S.sgr[m] = dq[m] * dchi_r * scale - g0 / (2.0 * r);
+        S.sgz[m] = dq[m] * dchi_z * scale;
+      }
       if (!kz) {
         for (int e = tid; e <= M2; e += NT) {
           const double rho = sqrt(dr * dr + c * c + 4.0 * r * rt * S.s2tab[e]);
@@ -359,10 +378,18 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
           S.fs[2][e] = q3_d(x);
         }
       }
-      for (int m = tid; m <= N; m += NT) sincos(m * alpha, &S.sma[m], &S.cma[m]);
+      for (int m = tid; m <= N + 1; m += NT) sincos(m * alpha, &S.sma[m], &S.cma[m]);
+      const int ip = S.qp[b0 + bi];
+      if (tid < order) {
+        const double xs = (s - (-M_PI / 2 + pw * ip)) / pw * 2.0 - 1.0;  // panel coordinate
+        double v = 1.0;
+        for (int mm = 0; mm < order; ++mm)
+          if (mm != tid) v *= (xs - gl_x[mm]) / (gl_x[tid] - gl_x[mm]);
+        S.pl[tid] = v;
+      }
       __syncthreads();
-      // C1: cosine coefficients f^_n = (2pi/M)[f_0 + (-1)^n f_{M/2} + 2 sum f_q cos(2 pi n q/M)]
       if (!kz) {
+        // C1: cosine coefficients f^_n = (2pi/M)[f_0 + (-1)^n f_{M/2} + 2 sum f_q cos(2 pi n q/M)]
         for (int e = tid; e < 3 * (n1 + 2); e += NT) {
           const int fn = e / (n1 + 2), n = e % (n1 + 2);
           const double* f = S.fs[fn];
@@ -394,20 +421,20 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         const int comp = e / (N + 2), m = e % (N + 2);
         double re, im = 0.0;
         if (kz) {
-          const double g0 = q[m] * scale;
-          re = comp == 0 ? g0 : (comp == 1 ? dq[m] * dchi_r * scale - g0 / (2.0 * r) : dq[m] * dchi_z * scale);
+          re = comp == 0 ? S.sg0[m] : (comp == 1 ? S.sgr[m] : S.sgz[m]);
         } else {
           double sum = 0.0;
-          for (int n = -n1; n <= n1; ++n) {
-            const int an = n < 0 ? -n : n;
-            const int am = (m - n) < 0 ? n - m : m - n;
-            const double g0 = q[am] * scale;
-            if (comp == 0) {
-              sum += S.fc[0][an] * g0;
-            } else if (comp == 1) {
-              sum += S.fc[0][an] * (dq[am] * dchi_r * scale - g0 / (2.0 * r)) + S.hr[an] * g0;
-            } else {
-              sum += S.fc[0][an] * (dq[am] * dchi_z * scale) + S.hz[an] * g0;
+          if (comp == 0) {
+            for (int n = -n1; n <= n1; ++n) sum += S.fc[0][abs(n)] * S.sg0[abs(m - n)];
+          } else if (comp == 1) {
+            for (int n = -n1; n <= n1; ++n) {
+              const int an = abs(n), am = abs(m - n);
+              sum += S.fc[0][an] * S.sgr[am] + S.hr[an] * S.sg0[am];
+            }
+          } else {
+            for (int n = -n1; n <= n1; ++n) {
+              const int an = abs(n), am = abs(m - n);
+              sum += S.fc[0][an] * S.sgz[am] + S.hz[an] * S.sg0[am];
             }
           }
           re = sum / (2.0 * M_PI);
@@ -416,101 +443,101 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         S.gre[comp][m] = re;
         S.gim[comp][m] = im;
       }
-      // E (part): Lagrange basis P_l(s)
-      const int ip = S.qp[b0 + bi];
-      if (tid < order) {
-        const double xs = (s - (-M_PI / 2 + pw * ip)) / pw * 2.0 - 1.0;  // panel coordinate
-        double v = 1.0;
-        for (int mm = 0; mm < order; ++mm)
-          if (mm != tid) v *= (xs - gl_x[mm]) / (gl_x[tid] - gl_x[mm]);
-        S.pl[tid] = v;
-      }
       __syncthreads();
-      // E: W_j = (1/2N)[G_0 + 2 sum_{m<N} G_m cos m(theta_j - alpha) + G_N cos N(theta_j - alpha)]
-      // for G, d_r G, d_z G, and for d_r G cos(phi) (coefficients (g_{m-1}+g_{m+1})/2);
-      // the odd part d_r G sin(phi) (coefficients (g_{m-1}-g_{m+1})/2i) gives
-      // (1/2N) sum_{m=1}^{N} f_m (g_{m-1} - g_{m+1}) sin m(theta_j - alpha), f_N = 1/2.
-      for (int e = tid; e < 5 * nth; e += NT) {
-        const int comp = e / nth, j = e % nth;
-        const int src = comp < 3 ? comp : 1;
-        const double* gr = S.gre[src];
-        const double* gi = S.gim[src];
-        double sre, sim;
-        if (comp == 3) {
-          sre = gr[1];
-          sim = gi[1];
-        } else if (comp == 4) {
-          sre = sim = 0.0;
-        } else {
-          sre = gr[0];
-          sim = gi[0];
-        }
-        int idx = 0;
-        for (int m = 1; m <= N; ++m) {
-          idx += j;
-          if (idx >= nth) idx -= nth;
-          double cr, ci, f;
-          if (comp == 4) {
-            const double sm = S.sth[idx] * S.cma[m] - S.cth[idx] * S.sma[m];  // sin m(theta_j - alpha)
-            f = (m < N ? 1.0 : 0.5) * sm;
-            cr = gr[m - 1] - gr[m + 1];
-            ci = gi[m - 1] - gi[m + 1];
-          } else {
-            const double cm = S.cth[idx] * S.cma[m] + S.sth[idx] * S.sma[m];  // cos m(theta_j - alpha)
-            f = (m < N) ? 2.0 * cm : cm;
-            cr = comp == 3 ? 0.5 * (gr[m - 1] + gr[m + 1]) : gr[m];
-            ci = comp == 3 ? 0.5 * (gi[m - 1] + gi[m + 1]) : gi[m];
-          }
-          sre += f * cr;
-          sim += f * ci;
-        }
-        S.wre[comp][j] = sre / nth;
-        S.wim[comp][j] = sim / nth;
-      }
-      __syncthreads();
-      // F: accumulate w P_l(s) [F^D_j + |J_lj| F^S_j]
-      const double wq = S.qw[b0 + bi];
-      const int base = ip * per_panel;
+      // E: theta-coefficients, index m = -N+1..N stored at m mod 2N (the entry at N is the
+      // symmetric Nyquist average), of
+      //   double layer  r l' (K^r - kappa r K^r cos theta) - r r' K^z,
+      //   single layer  -i eta G,
+      // with K(theta - alpha) -> k^_|m| e^{-i m alpha} and cos(theta) averaging m -+ 1.
       const double rl = r * sc[9], kr = sc[11], rrp = r * sc[10];
-      double sal, cal;
-      sincos(alpha, &sal, &cal);
-      for (int e = tid; e < per_panel; e += NT) {
-        const int l = e / nth, j = e % nth;
-        const double J = jac[B.offset + base + e];
-        const double rcre = cal * S.wre[3][j] - sal * S.wre[4][j];  // int d_r G cos(theta) L_j
-        const double rcim = cal * S.wim[3][j] - sal * S.wim[4][j];
-        const double fre = rl * (S.wre[1][j] - kr * rcre) - rrp * S.wre[2][j] + J * eta * S.wim[0][j];
-        const double fim = rl * (S.wim[1][j] - kr * rcim) - rrp * S.wim[2][j] - J * eta * S.wre[0][j];
-        const double f = wq * S.pl[l];
-        acc[base + e].x += f * fre;
-        acc[base + e].y += f * fim;
+      for (int mm = tid; mm < nth; mm += NT) {
+        const int m0 = mm <= N ? mm : mm - nth;
+        const int nsum = (m0 == N) ? 2 : 1;
+        const double fac = (nsum == 2) ? 0.5 : 1.0;
+        double dre_ = 0.0, dimv = 0.0, tre_ = 0.0, timv = 0.0;
+        for (int sgn = 0; sgn < nsum; ++sgn) {
+          const int m = (sgn == 0) ? m0 : -N;
+          const int a0 = abs(m), am1 = abs(m - 1), ap1 = abs(m + 1);
+          // e^{-i mv alpha} = cos(|mv| alpha) -/+ i sin(|mv| alpha)
+          const double c0r = S.cma[a0], c0i = m >= 0 ? -S.sma[a0] : S.sma[a0];
+          const double cmr = S.cma[am1], cmi = (m - 1) >= 0 ? -S.sma[am1] : S.sma[am1];
+          const double cpr = S.cma[ap1], cpi = (m + 1) >= 0 ? -S.sma[ap1] : S.sma[ap1];
+          const double krr = S.gre[1][a0] * c0r - S.gim[1][a0] * c0i, kri = S.gre[1][a0] * c0i + S.gim[1][a0] * c0r;
+          const double kzr = S.gre[2][a0] * c0r - S.gim[2][a0] * c0i, kzi = S.gre[2][a0] * c0i + S.gim[2][a0] * c0r;
+          const double g0r = S.gre[0][a0] * c0r - S.gim[0][a0] * c0i, g0i = S.gre[0][a0] * c0i + S.gim[0][a0] * c0r;
+          const double kmr = S.gre[1][am1] * cmr - S.gim[1][am1] * cmi, kmi = S.gre[1][am1] * cmi + S.gim[1][am1] * cmr;
+          const double kpr = S.gre[1][ap1] * cpr - S.gim[1][ap1] * cpi, kpi = S.gre[1][ap1] * cpi + S.gim[1][ap1] * cpr;
+          const double kcr = 0.5 * (kmr + kpr), kci = 0.5 * (kmi + kpi);  // (K^r cos theta)^_m
+          dre_ += fac * (rl * (krr - kr * kcr) - rrp * kzr);
+          dimv += fac * (rl * (kri - kr * kci) - rrp * kzi);
+          tre_ += fac * (eta * g0i);
+          timv += fac * (-eta * g0r);
+        }
+        S.dre[mm] = dre_;
+        S.dim_[mm] = dimv;
+        S.tre[mm] = tre_;
+        S.tim[mm] = timv;
       }
       __syncthreads();
+      // F: accumulate w P_l(s) x (theta-coefficients) for the node's panel
+      const double wq = S.qw[b0 + bi];
+      for (int e = tid; e < per_panel; e += NT) {
+        const int l = e / nth, mm = e % nth;
+        const double f = wq * S.pl[l];
+        accD[e].x += f * S.dre[mm];
+        accD[e].y += f * S.dim_[mm];
+        accS[e].x += f * S.tre[mm];
+        accS[e].y += f * S.tim[mm];
+      }
+      __syncthreads();
+      // panel finished: inverse DFT of the accumulated coefficients into the row,
+      //   A[t,(ip,l,j)] = (1/2N) sum_m [D_lm + |J_lj| S_lm] e^{i m theta_j}
+      const int gidx = b0 + bi;
+      if (gidx == nq - 1 || S.qp[gidx + 1] != ip) {
+        const int base = ip * per_panel;
+        for (int e = tid; e < per_panel; e += NT) {
+          const int l = e / nth, j = e % nth;
+          const double J = jac[B.offset + base + e];
+          double sr = 0.0, si = 0.0;
+          int idx = 0;
+          for (int mm = 0; mm < nth; ++mm) {
+            // e^{i m theta_j} with m = mm or mm - 2N (the same value): table[(mm j) mod 2N]
+            const double cr = S.cth[idx], ci = S.sth[idx];
+            const double ar = accD[l * nth + mm].x + J * accS[l * nth + mm].x;
+            const double ai = accD[l * nth + mm].y + J * accS[l * nth + mm].y;
+            sr += ar * cr - ai * ci;
+            si += ar * ci + ai * cr;
+            idx += j;
+            if (idx >= nth) idx -= nth;
+          }
+          double2 v = make_double2(sr / nth, si / nth);
+          if (base + e == t) v.x += 0.5;
+          row[base + e] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_double2(0.0, 0.0);
+        __syncthreads();
+      }
     }
   }
-  // write the row: near panels from the accumulator times |J|, far panels by the plain rule
-  double2* row = blocks + B.blk + (long long)t * nbn;
+  // panels beyond the neighbours: the plain smooth rule
   const qd4 xt = x64[g];
   for (int e = tid; e < nbn; e += NT) {
     const int i = e / per_panel;
+    if (abs(i - p) <= 1) continue;
     const long long src = B.offset + e;
-    double2 v;
-    if (abs(i - p) <= 1) {
-      v = acc[e];
-    } else {
-      double kre, kim;
-      smooth_kernel(xt, x64[src], n64[src], k, eta, &kre, &kim);
-      const double w = x64[src].w;
-      v = make_double2(kre * w, kim * w);
-    }
-    if (e == t) v.x += 0.5;
-    row[e] = v;
+    double kre, kim;
+    smooth_kernel(xt, x64[src], n64[src], k, eta, &kre, &kim);
+    const double w = x64[src].w;
+    row[e] = make_double2(kre * w, kim * w);
   }
 }
 
 }  // namespace
 
-size_t qams_selfblock_smem(int max_nb) { return sizeof(RowShared) + sizeof(double2) * (size_t)max_nb; }
+static_assert(sizeof(RowShared) % 16 == 0, "double2 accumulators follow RowShared");
+
+size_t qams_selfblock_smem(int max_per_panel) { return sizeof(RowShared) + 2 * sizeof(double2) * (size_t)max_per_panel; }
 
 int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   const int nb = (int)c->bodies.size();
@@ -552,6 +579,11 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
       for (auto& v : w) v *= 0.5;
       rules.insert(rules.end(), x.begin(), x.end());
       rules.insert(rules.end(), w.begin(), w.end());
+      qams_gauss_legendre(12, x, w);
+      for (auto& v : x) v = 0.5 * (v + 1.0);
+      for (auto& v : w) v *= 0.5;
+      rules.insert(rules.end(), x.begin(), x.end());
+      rules.insert(rules.end(), w.begin(), w.end());
     }
     AsmBody& A = ab[b];
     A.n_panels = d.n_panels;
@@ -576,7 +608,7 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
     if (A.n1 + 2 > MAXN1 || A.M / 2 + 1 > MAXM2 || d.n_theta / 2 + A.n1 + 2 > MAXP || 2 * A.M > 4 * MAXM2)
       return QAMS_EINVAL;
     A.rule = rule_off[d.order];
-    max_nb = std::max(max_nb, bh.n);
+    max_nb = std::max(max_nb, d.order * d.n_theta);
   }
   int rc;
   qams_dev_free(c, &c->blocks64);

@@ -165,6 +165,20 @@ def assembly_flops(scene):
     return total
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """Largest value of x over all ranks (the job is as slow as its slowest rank)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(pair_evals_per_rank: float, world: int, elapsed_max: float) -> float:
+    """Whole-job pair-interactions/s: every rank solves its own request of the
+    same size (replicas, weak scaling), timed by the slowest rank."""
+    return pair_evals_per_rank * world / elapsed_max
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -230,9 +244,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     elapsed = t0.elapsed_time(t1) / 1e3
     if dist:
-        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+        elapsed = max_over_ranks(elapsed, dist, "cuda")
         dist.barrier()
     step_ms = [r[0][0].elapsed_time(r[0][3]) for r in recs]
     asm_ms = [r[0][0].elapsed_time(r[0][1]) for r in recs]
@@ -240,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
     ff_ms = [r[0][2].elapsed_time(r[0][3]) for r in recs]
     applies = [r[1]["applies_fp32"] + r[1]["applies_fp64"] for r in recs]
     pair_evals = sum(a * pairs * R for a in applies)
-    value = pair_evals * world / elapsed  # every rank solves its own request of the same size
+    value = job_value(pair_evals, world, elapsed)
 
     # accuracy of the mixed result against the plain FP64 GPU solve of the same scene
     mu64 = torch.zeros_like(b)
@@ -396,6 +408,51 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(args):
+    """Serving stream: seeded requests with 10..max_bodies bodies, {16x32, 24x48}
+    nodes, k ~ U[1, 15], 1..16 RHS, each a full mixed solve to 1e-11 plus 400
+    far-field directions.  A burst (all requests at once) measures the
+    saturated rate; Poisson arrivals at 0.8 of it give the latency distribution."""
+    import numpy as np
+
+    import paper_2606_31380_b300 as q
+    import scenes
+
+    reqs = [scenes.serving_request(i, max_bodies=args.serve_max_bodies) for i in range(args.serve_requests)]
+    far = scenes.fibonacci_directions(400)
+    srv = q.Server(0, 0, slots=args.serve_slots)
+    srv.wait(srv.submit(reqs[0], far))  # warm-up
+    t0 = time.perf_counter()
+    tickets = [srv.submit(r, far) for r in reqs]
+    burst = [srv.wait(t) for t in tickets]
+    t_burst = time.perf_counter() - t0
+    sat = len(reqs) / t_burst
+    rng = np.random.default_rng(31380)
+    lam = 0.8 * sat
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
+    t0 = time.perf_counter()
+    tickets = []
+    for r, at in zip(reqs, arrivals):
+        dt = at - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(r, far))
+    res = [srv.wait(t) for t in tickets]
+    t_stream = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = all(r["status"] == 0 for r in res + burst)
+    out = {"metric": "serving solves/s and p50/p99 solve latency", "value": len(reqs) / t_stream,
+           "unit": "solves/s", "higher_is_better": True, "n_gpus": 1, "data": "synthetic (seeded requests)",
+           "config": {"workload": f"{len(reqs)} requests, 10..{args.serve_max_bodies} bodies, "
+                                  "{16x32, 24x48} nodes, k ~ U[1,15], 1..16 RHS, tol 1e-11",
+                      "slots": args.serve_slots, "arrival_rate_per_s": lam},
+           "saturated_solves_per_s": sat, "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                                         "p99": float(np.percentile(lat, 99))},
+           "mean_nodes": float(np.mean([r["n_nodes"] for r in res])), "all_ok": ok}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,11 +463,18 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bodies", type=int, default=0, help="use only the first B bodies (small profiling case)")
+    ap.add_argument("--serve", action="store_true", help="serving stream instead of the single-solve step")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-max-bodies", type=int, default=40)
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.serve:
+        if rank == 0:
+            run_serve(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)

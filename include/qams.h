@@ -47,7 +47,8 @@ enum {
   QAMS_ETIMEOUT = -6,   /* a bounded device wait gave up                  */
   QAMS_ECANCELLED = -7, /* cancelled between restart cycles               */
   QAMS_ECUDA = -8,      /* a CUDA runtime call failed                     */
-  QAMS_ESCRATCH = -9    /* problem too large for the static scratch       */
+  QAMS_ESCRATCH = -9,   /* problem too large for the static scratch       */
+  QAMS_EAGAIN = -10     /* request not finished yet (qams_poll)           */
 };
 
 enum { QAMS_PREC_FP64 = 0, QAMS_PREC_FP32 = 1 };
@@ -134,6 +135,20 @@ int qams_assemble(qams_ctx* ctx, void* stream);
  * rows = targets, columns = sources, both in node order) to dst_dev. */
 int qams_copy_selfblock(const qams_ctx* ctx, int body, void* dst_dev, void* stream);
 
+/* Block-Jacobi preconditioner (Sec. 6: GMRES with a block-diagonal
+ * preconditioner from the factorisation of the self matrix): P_b = A_b^{-1}
+ * for every body, by blocked Gauss-Jordan elimination in complex64 (pivot
+ * blocks of 64 inverted with partial pivoting, rank-64 updates as batched
+ * complex64 GEMMs), kept library-owned in complex64 and widened to
+ * complex128.  Requires qams_assemble; invalidated by the next assembly.
+ * Blocking.  Errors: QAMS_EINVAL, QAMS_ENUMERIC (a vanishing pivot),
+ * QAMS_EBUDGET, QAMS_ECUDA. */
+int qams_build_preconditioner(qams_ctx* ctx, void* stream);
+
+/* Copy body `body`'s preconditioner block P_b (row-major n_b x n_b
+ * complex128) to dst_dev. */
+int qams_copy_preconditioner(const qams_ctx* ctx, int body, void* dst_dev, void* stream);
+
 /* Operator apply (Eq. linearsys): y = (1/2 I + D - i eta S) x for [N][R]
  * complex x (densities mu, weights not folded in), self blocks times x
  * plus the inter-body pair sum of w x.  QAMS_PREC_FP64 works in complex128,
@@ -148,8 +163,12 @@ int qams_apply(qams_ctx* ctx, int R, const void* x_dev, void* y_dev, int precisi
  * A d = r by GMRES with the FP32 apply to a relative reduction inner_tol,
  * then mu += d and r = b - A mu with the FP64 apply, until r meets tol.  The
  * Krylov basis and Gram-Schmidt (classical, applied twice) are FP64 in both
- * modes.  qams_solve_opts_default fills: FP32, restart 50, max_iters 1000,
- * tol 1e-11, inner_tol 1e-5, max_refine 12. */
+ * modes.  With precondition = 1 GMRES runs on A P^{-1} with the block-
+ * Jacobi preconditioner of qams_build_preconditioner (built by the first
+ * solve that asks for it) and returns mu = P^{-1} z.  A cancelled server
+ * request stops between restart cycles with QAMS_ECANCELLED.
+ * qams_solve_opts_default fills: FP32, restart 50, max_iters 1000,
+ * tol 1e-11, inner_tol 1e-5, max_refine 12, precondition 1. */
 typedef struct {
   int precision;
   int restart;      /* m, 1..200 */
@@ -157,6 +176,7 @@ typedef struct {
   double tol;       /* on ||b - A mu|| / ||b|| (FP64 residual) */
   double inner_tol; /* FP32 mode: reduction per correction */
   int max_refine;   /* FP32 mode: corrections */
+  int precondition; /* 1: right block-Jacobi preconditioning (built on first use) */
 } qams_solve_opts;
 
 typedef struct {
@@ -220,6 +240,63 @@ int qams_incident_plane(qams_ctx* ctx, int R, const double* dirs_host, void* rhs
  * uinf_dev is [M][R] complex128. */
 int qams_farfield(qams_ctx* ctx, int R, const void* mu_dev, int M, const double* dirs_host,
                   void* uinf_dev, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop over independent scattering problems (the
+ * paper solves one problem at a time).  Each request is a full solve -- its
+ * own bodies, wavenumber and incident directions.  Requests are admitted
+ * while their estimated device footprint fits in the server's HBM budget
+ * and a slot is free; every admitted request runs on its own CUDA stream
+ * with its own library context, so requests that arrive while others are on
+ * the GPU start as soon as a slot and memory free up and their kernels
+ * overlap on the device (continuous batching).  The kernels are
+ * deterministic, so a request's result does not depend on what else runs.
+ * ------------------------------------------------------------------------ */
+typedef struct qams_server qams_server; /* opaque */
+
+typedef struct {
+  int n_bodies;
+  const qams_body_desc* bodies; /* copied at submit */
+  double k, eta;
+  int R;                        /* right-hand sides, 1..16 */
+  const double* dirs;           /* [R][3] incident directions, copied */
+  int M;                        /* far-field directions (0 = none) */
+  const double* far_dirs;       /* [M][3], copied */
+  int precision;                /* QAMS_PREC_FP64 or QAMS_PREC_FP32 (refined) */
+  double tol;                   /* relative residual target */
+  double* mu_host;              /* optional [N][R] complex128 output (caller-owned, valid until done) */
+  double* uinf_host;            /* optional [M][R] complex128 output (caller-owned, valid until done) */
+} qams_request;
+
+typedef struct {
+  int status;           /* QAMS_OK or the request's error code */
+  long long n_nodes;
+  int iterations, refinements;
+  double rel_residual;
+  double queue_ms;      /* submit -> admission        */
+  double run_ms;        /* admission -> completion    */
+  double latency_ms;    /* submit -> completion       */
+  size_t footprint;     /* admitted footprint estimate */
+} qams_result;
+
+/* Device bytes a solve of these bodies with R right-hand sides and restart m
+ * holds: node tables, self blocks (complex128 + complex64), preconditioner
+ * (complex64 + complex128), Krylov basis and workspaces.  Host only. */
+int qams_footprint(const qams_body_desc* bodies, int n_bodies, int R, int restart, size_t* bytes);
+
+/* Start a server on CUDA device `cuda_device` with `max_slots` concurrent
+ * requests and an HBM budget (0 = 90% of the device's free memory now). */
+int qams_server_create(qams_server** out, int cuda_device, size_t hbm_budget, int max_slots);
+/* Drops queued requests, waits for running ones, frees everything. */
+void qams_server_destroy(qams_server* s);
+/* Non-blocking.  QAMS_EBUDGET when the request could never fit the budget. */
+int qams_submit(qams_server* s, const qams_request* req, uint64_t* ticket);
+/* QAMS_EAGAIN while queued or running; otherwise fills *result and forgets
+ * the ticket (returns QAMS_OK even when result->status is an error). */
+int qams_poll(qams_server* s, uint64_t ticket, qams_result* result);
+/* Queued: dropped at once.  Running: stops at the next GMRES restart
+ * boundary; the result then has status QAMS_ECANCELLED. */
+int qams_cancel(qams_server* s, uint64_t ticket);
 
 #ifdef __cplusplus
 }

@@ -20,12 +20,24 @@ def lib_path() -> str:
 
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int), ("tol", C.c_double),
-                ("inner_tol", C.c_double), ("max_refine", C.c_int)]
+                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("precondition", C.c_int)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double),
                 ("solve_ms", C.c_double), ("applies_fp32", C.c_int), ("applies_fp64", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("n_bodies", C.c_int), ("bodies", C.c_void_p), ("k", C.c_double), ("eta", C.c_double),
+                ("R", C.c_int), ("dirs", C.c_void_p), ("M", C.c_int), ("far_dirs", C.c_void_p),
+                ("precision", C.c_int), ("tol", C.c_double), ("mu_host", C.c_void_p), ("uinf_host", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_nodes", C.c_longlong), ("iterations", C.c_int), ("refinements", C.c_int),
+                ("rel_residual", C.c_double), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("latency_ms", C.c_double), ("footprint", C.c_size_t)]
 
 
 class BodyDesc(C.Structure):
@@ -64,6 +76,14 @@ def load_library():
         "qams_assemble": (i, [vp, vp]),
         "qams_copy_selfblock": (i, [vp, i, vp, vp]),
         "qams_apply": (i, [vp, i, vp, vp, i, vp]),
+        "qams_build_preconditioner": (i, [vp, vp]),
+        "qams_footprint": (i, [vp, i, i, i, C.POINTER(C.c_size_t)]),
+        "qams_server_create": (i, [C.POINTER(vp), i, C.c_size_t, i]),
+        "qams_server_destroy": (None, [vp]),
+        "qams_submit": (i, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        "qams_poll": (i, [vp, C.c_uint64, C.POINTER(Result)]),
+        "qams_cancel": (i, [vp, C.c_uint64]),
+        "qams_copy_preconditioner": (i, [vp, i, vp, vp]),
         "qams_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
         "qams_pairsum_f32_static": (i, [i, vp, vp, vp, vp, i, vp, vp, d, d, vp]),
         "qams_solve": (i, [vp, i, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveStats), vp]),
@@ -202,6 +222,16 @@ class Context:
         _check(self.lib.qams_copy_selfblock(self._h, body, _dev(dst, torch.complex128, (n, n), "dst"),
                                             C.c_void_p(_stream_ptr(stream))), "qams_copy_selfblock")
 
+    def build_preconditioner(self, stream=None):
+        _check(self.lib.qams_build_preconditioner(self._h, C.c_void_p(_stream_ptr(stream))),
+               "qams_build_preconditioner")
+
+    def copy_preconditioner(self, body: int, dst, stream=None):
+        import torch
+        n = int(self.body_offsets()[body + 1] - self.body_offsets()[body])
+        _check(self.lib.qams_copy_preconditioner(self._h, body, _dev(dst, torch.complex128, (n, n), "dst"),
+                                                 C.c_void_p(_stream_ptr(stream))), "qams_copy_preconditioner")
+
     def apply(self, x, y, precision: int = PREC_FP64, stream=None):
         import torch
         R = x.shape[1]
@@ -210,7 +240,8 @@ class Context:
                                    precision, C.c_void_p(_stream_ptr(stream))), "qams_apply")
 
     def solve(self, rhs, mu, precision: int = PREC_FP32, tol: float = None, restart: int = None,
-              max_iters: int = None, inner_tol: float = None, stream=None, check: bool = True):
+              max_iters: int = None, inner_tol: float = None, precondition: bool = True, stream=None,
+              check: bool = True):
         """Solve A mu = rhs; returns a dict of solver statistics."""
         import torch
         R = rhs.shape[1]
@@ -227,6 +258,7 @@ class Context:
             o.max_iters = max_iters
         if inner_tol is not None:
             o.inner_tol = inner_tol
+        o.precondition = 1 if precondition else 0
         st = SolveStats()
         code = self.lib.qams_solve(self._h, R, _dev(rhs, torch.complex128, (self.N, R), "rhs"),
                                    _dev(mu, torch.complex128, (self.N, R), "mu"), C.byref(o), C.byref(st),
@@ -255,3 +287,79 @@ class Context:
                                       dirs.ctypes.data_as(C.c_void_p),
                                       _dev(uinf, torch.complex128, (M, R), "uinf"),
                                       C.c_void_p(_stream_ptr(stream))), "qams_farfield")
+
+
+QAMS_EAGAIN = -10
+
+
+def footprint(bodies, R: int, restart: int = 50) -> int:
+    """Device bytes a solve of these bodies holds (host-side estimate)."""
+    lib = load_library()
+    arr, keep = body_desc_array(bodies)
+    out = C.c_size_t()
+    _check(lib.qams_footprint(C.cast(arr, C.c_void_p), len(bodies), R, restart, C.byref(out)), "qams_footprint")
+    return int(out.value)
+
+
+class Server:
+    """The library's request loop: admission by device footprint, one stream per
+    admitted request, requests overlapping on the GPU."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, slots: int = 4):
+        self.lib = load_library()
+        self._h = C.c_void_p()
+        _check(self.lib.qams_server_create(C.byref(self._h), device, hbm_budget, slots), "qams_server_create")
+        self._keep = {}
+
+    def close(self):
+        if self._h:
+            self.lib.qams_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, scene, far_dirs=None, precision: int = PREC_FP32, tol: float = 1e-11, want_mu: bool = True):
+        """Queue one scene; returns a ticket.  Outputs land in host arrays returned by poll()."""
+        arr, keep = body_desc_array(scene.bodies)
+        dirs = np.ascontiguousarray(scene.directions, float)
+        R = dirs.shape[0]
+        N = scene.n_nodes
+        fd = None if far_dirs is None else np.ascontiguousarray(far_dirs, float)
+        M = 0 if fd is None else fd.shape[0]
+        mu = np.zeros((N, R), complex) if want_mu else None
+        uinf = np.zeros((M, R), complex) if M else None
+        req = Request(len(scene.bodies), C.cast(arr, C.c_void_p), scene.k, scene.eta, R,
+                      dirs.ctypes.data_as(C.c_void_p), M, None if fd is None else fd.ctypes.data_as(C.c_void_p),
+                      precision, tol, None if mu is None else mu.ctypes.data_as(C.c_void_p),
+                      None if uinf is None else uinf.ctypes.data_as(C.c_void_p))
+        t = C.c_uint64()
+        _check(self.lib.qams_submit(self._h, C.byref(req), C.byref(t)), "qams_submit")
+        self._keep[t.value] = (arr, keep, dirs, fd, mu, uinf)
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """None while queued or running; else a dict with status, stats, mu and uinf."""
+        res = Result()
+        code = self.lib.qams_poll(self._h, C.c_uint64(ticket), C.byref(res))
+        if code == QAMS_EAGAIN:
+            return None
+        _check(code, "qams_poll")
+        _, _, _, _, mu, uinf = self._keep.pop(ticket)
+        return dict(status=res.status, n_nodes=res.n_nodes, iterations=res.iterations,
+                    refinements=res.refinements, rel_residual=res.rel_residual, queue_ms=res.queue_ms,
+                    run_ms=res.run_ms, latency_ms=res.latency_ms, footprint=res.footprint, mu=mu, uinf=uinf)
+
+    def wait(self, ticket: int, poll_s: float = 0.005):
+        import time
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            time.sleep(poll_s)
+
+    def cancel(self, ticket: int):
+        _check(self.lib.qams_cancel(self._h, C.c_uint64(ticket)), "qams_cancel")

@@ -135,6 +135,16 @@ int qams_block_apply(qams_ctx* c, int R, const void* x, void* y, int precision, 
   return QAMS_OK;
 }
 
+int qams_block_apply_ptr(qams_ctx* c, const void* blocks, int R, const void* x, void* y, int precision,
+                         bool accumulate, cudaStream_t st) {
+  if (precision == QAMS_PREC_FP64)
+    block_dispatch<double2>(c, blocks, x, y, R, accumulate ? 1 : 0, st);
+  else
+    block_dispatch<float2>(c, blocks, x, y, R, accumulate ? 1 : 0, st);
+  QAMS_CUDA(cudaGetLastError());
+  return QAMS_OK;
+}
+
 int qams_apply_launch(qams_ctx* c, int R, const void* x, void* y, int precision, cudaStream_t st) {
   const size_t need = sizeof(double2) * (size_t)c->N * R;
   if (c->ws_sigma.bytes < need) {

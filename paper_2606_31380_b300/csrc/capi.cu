@@ -37,7 +37,7 @@ void qams_dev_free(qams_ctx* c, DeviceBuf* b) {
 qams_ctx::~qams_ctx() {
   cudaSetDevice(device);
   for (DeviceBuf* b : {&x64, &n64, &x32, &n32, &centers, &boff, &jac64, &d_tiles, &d_splits, &partial,
-                        &blocks64, &blocks32, &blk_off, &ws_sigma, &ws_y})
+                        &blocks64, &blocks32, &blk_off, &ws_sigma, &ws_y, &pinv32, &pinv64})
     qams_dev_free(this, b);
 }
 
@@ -57,6 +57,7 @@ const char* qams_strerror(int code) {
     case QAMS_ECANCELLED: return "cancelled";
     case QAMS_ECUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
     case QAMS_ESCRATCH: return "problem exceeds the static scratch of the no-allocation entry point";
+    case QAMS_EAGAIN: return "request not finished yet";
     default: return "unknown error";
   }
 }
@@ -109,9 +110,10 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
     }
   QAMS_CUDA(cudaSetDevice(c->device));
   for (DeviceBuf* b : {&c->x64, &c->n64, &c->x32, &c->n32, &c->centers, &c->boff, &c->jac64, &c->blocks64,
-                       &c->blocks32, &c->blk_off, &c->ws_sigma, &c->ws_y})
+                       &c->blocks32, &c->blk_off, &c->ws_sigma, &c->ws_y, &c->pinv32, &c->pinv64})
     qams_dev_free(c, b);
   c->assembled = false;
+  c->have_precond = false;
   c->bodies = std::move(bh);
   int rc = qams_build_nodes(c);
   if (rc) return rc;
@@ -200,6 +202,7 @@ int qams_assemble(qams_ctx* c, void* stream) {
   if (!c || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
   QAMS_CUDA(cudaSetDevice(c->device));
   c->assembled = false;
+  c->have_precond = false;
   int rc = qams_assemble_launch(c, (cudaStream_t)stream);
   if (rc) return rc;
   rc = qams_blocks_to_fp32(c, (cudaStream_t)stream);
@@ -215,6 +218,27 @@ int qams_copy_selfblock(const qams_ctx* c, int body, void* dst, void* stream) {
   const long long n = c->bodies[body].n;
   QAMS_CUDA(cudaSetDevice(c->device));
   QAMS_CUDA(cudaMemcpyAsync(dst, (const double2*)c->blocks64.p + off, sizeof(double2) * n * n,
+                            cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return QAMS_OK;
+}
+
+int qams_build_preconditioner(qams_ctx* c, void* stream) {
+  if (!c || !c->assembled) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  c->have_precond = false;
+  int rc = qams_precond_launch(c, (cudaStream_t)stream);
+  if (rc) return rc;
+  c->have_precond = true;
+  return QAMS_OK;
+}
+
+int qams_copy_preconditioner(const qams_ctx* c, int body, void* dst, void* stream) {
+  if (!c || !c->have_precond || body < 0 || body >= (int)c->bodies.size() || !dst) return QAMS_EINVAL;
+  long long off = 0;
+  for (int b = 0; b < body; ++b) off += (long long)c->bodies[b].n * c->bodies[b].n;
+  const long long n = c->bodies[body].n;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  QAMS_CUDA(cudaMemcpyAsync(dst, (const double2*)c->pinv64.p + off, sizeof(double2) * n * n,
                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return QAMS_OK;
 }

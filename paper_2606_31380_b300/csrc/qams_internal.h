@@ -57,6 +57,7 @@ struct qams_ctx {
   long long N = 0;
   double k = 0.0, eta = 1.0;
   bool have_k = false;
+  const int* cancel = nullptr;  // set by the server: checked between GMRES restart cycles
 
   // host node tables (FP64, world frame)
   std::vector<double> hx, hn, hw, hj;  // [N][3], [N][3], [N], [N] (|J|)
@@ -76,6 +77,11 @@ struct qams_ctx {
   DeviceBuf blk_off;   // long long [nb+1]: first entry of each block
   long long block_entries = 0;
   bool assembled = false;
+
+  // block-Jacobi preconditioner: inverses of the self blocks (same layout)
+  DeviceBuf pinv32;  // complex64, computed
+  DeviceBuf pinv64;  // complex128 widening of pinv32 (an exact linear map for the FP64 path)
+  bool have_precond = false;
 
   // apply workspaces
   DeviceBuf ws_sigma, ws_y;
@@ -107,6 +113,11 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st);
 int qams_blocks_to_fp32(qams_ctx* c, cudaStream_t st);
 int qams_block_apply(qams_ctx* c, int R, const void* x, void* y, int precision, bool accumulate, cudaStream_t st);
 int qams_apply_launch(qams_ctx* c, int R, const void* x, void* y, int precision, cudaStream_t st);
+int qams_block_apply_ptr(qams_ctx* c, const void* blocks, int R, const void* x, void* y, int precision,
+                         bool accumulate, cudaStream_t st);
+
+// precond.cu
+int qams_precond_launch(qams_ctx* c, cudaStream_t st);
 
 // fields.cu
 int qams_incident_launch(qams_ctx* c, int R, const double* dirs_host, void* rhs, cudaStream_t st);

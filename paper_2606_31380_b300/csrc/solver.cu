@@ -128,8 +128,9 @@ struct Solver {
   int R, m;
   long long N;
   cudaStream_t st;
-  DeviceBuf V, w, partial, hbuf, t32a, t32b;
+  DeviceBuf V, w, partial, hbuf, t32a, t32b, t32c, t64;
   std::vector<double2> hhost;
+  bool prec = false;  // right block-Jacobi preconditioning: the operator is A P^{-1}
 
   int init() {
     int rc;
@@ -139,25 +140,50 @@ struct Solver {
     if ((rc = qams_dev_alloc(c, &hbuf, sizeof(double2) * (size_t)(m + 1) * R))) return rc;
     if ((rc = qams_dev_alloc(c, &t32a, sizeof(float2) * (size_t)N * R))) return rc;
     if ((rc = qams_dev_alloc(c, &t32b, sizeof(float2) * (size_t)N * R))) return rc;
+    if ((rc = qams_dev_alloc(c, &t32c, sizeof(float2) * (size_t)N * R))) return rc;
+    if ((rc = qams_dev_alloc(c, &t64, sizeof(double2) * (size_t)N * R))) return rc;
     hhost.resize((size_t)(m + 1) * R);
     return QAMS_OK;
   }
   void release() {
-    for (DeviceBuf* b : {&V, &w, &partial, &hbuf, &t32a, &t32b}) qams_dev_free(c, b);
+    for (DeviceBuf* b : {&V, &w, &partial, &hbuf, &t32a, &t32b, &t32c, &t64}) qams_dev_free(c, b);
   }
   double2* Vi(int i) { return (double2*)V.p + (size_t)i * N * R; }
 
-  // y = A x with the requested operator precision (FP64 in and out)
+  // y = A x (or A P^{-1} x when preconditioned) with the requested operator
+  // precision; FP64 in and out
   int applies = 0;
   int op(const double2* x, double2* y, int precision) {
     ++applies;
-    if (precision == QAMS_PREC_FP64) return qams_apply_launch(c, R, x, y, QAMS_PREC_FP64, st);
+    int rc;
+    if (precision == QAMS_PREC_FP64) {
+      const double2* xin = x;
+      if (prec) {
+        if ((rc = qams_block_apply_ptr(c, c->pinv64.p, R, x, t64.p, QAMS_PREC_FP64, false, st))) return rc;
+        xin = (const double2*)t64.p;
+      }
+      return qams_apply_launch(c, R, xin, y, QAMS_PREC_FP64, st);
+    }
     const long long n = N * R;
     narrow_kernel<<<nblk(n), 256, 0, st>>>(x, (float2*)t32a.p, n); qams_count_launch();
-    int rc = qams_apply_launch(c, R, t32a.p, t32b.p, QAMS_PREC_FP32, st);
+    const void* xin = t32a.p;
+    if (prec) {
+      if ((rc = qams_block_apply_ptr(c, c->pinv32.p, R, t32a.p, t32c.p, QAMS_PREC_FP32, false, st))) return rc;
+      xin = t32c.p;
+    }
+    rc = qams_apply_launch(c, R, xin, t32b.p, QAMS_PREC_FP32, st);
     if (rc) return rc;
     widen_kernel<<<nblk(n), 256, 0, st>>>((const float2*)t32b.p, y, n); qams_count_launch();
     QAMS_CUDA(cudaGetLastError());
+    return QAMS_OK;
+  }
+
+  // x <- P^{-1} x (back from the preconditioned variable), FP64
+  int unprecondition(double2* x) {
+    if (!prec) return QAMS_OK;
+    int rc = qams_block_apply_ptr(c, c->pinv64.p, R, x, t64.p, QAMS_PREC_FP64, false, st);
+    if (rc) return rc;
+    QAMS_CUDA(cudaMemcpyAsync(x, t64.p, sizeof(double2) * (size_t)N * R, cudaMemcpyDeviceToDevice, st));
     return QAMS_OK;
   }
 
@@ -199,6 +225,7 @@ struct Solver {
       bool done = true;
       for (int r = 0; r < R; ++r) done = done && (bn[r] == 0 || beta[r] <= tol * bn[r]);
       if (done || it >= maxit) break;
+      if (c->cancel && __atomic_load_n(c->cancel, __ATOMIC_RELAXED)) return QAMS_ECANCELLED;
       // V0 = r / beta
       std::vector<double2> sc(R);
       for (int r = 0; r < R; ++r) sc[r] = make_double2(beta[r] > 0 ? 1.0 / beta[r] : 0.0, 0.0);
@@ -306,13 +333,24 @@ extern "C" int qams_solve(qams_ctx* c, int R, const void* rhs, void* mu, const q
   QAMS_CUDA(cudaEventCreate(&e1));
   QAMS_CUDA(cudaEventRecord(e0, st));
   Solver S{c, R, o.restart, c->N, st};
-  int rc = S.init();
+  int rc = QAMS_OK;
+  if (o.precondition && !c->have_precond) {
+    rc = qams_precond_launch(c, st);
+    if (rc) return rc;
+    c->have_precond = true;
+  }
+  S.prec = o.precondition != 0;
+  rc = S.init();
   qams_solve_stats s{};
   const long long n = c->N * R;
   if (!rc) {
     if (o.precision == QAMS_PREC_FP64) {
       rc = S.gmres((const double2*)rhs, (double2*)mu, QAMS_PREC_FP64, o.tol, o.max_iters, &s.iterations,
                    &s.rel_residual);
+      if (!rc || rc == QAMS_ENOCONV) {
+        const int rc2 = S.unprecondition((double2*)mu);
+        if (rc2) rc = rc2;
+      }
       s.refinements = 0;
     } else {
       // iterative refinement: x = 0, r = b; repeat d = GMRES_32(r), x += d, r = b - A_64 x
@@ -335,6 +373,7 @@ extern "C" int qams_solve(qams_ctx* c, int R, const void* rhs, void* mu, const q
                             std::max(1, o.max_iters - total), &its, &inner_rel);
           total += its;
           if (irc && irc != QAMS_ENOCONV) { rc = irc; break; }
+          if ((rc = S.unprecondition((double2*)dd.p))) break;
           add_kernel<<<nblk(n), 256, 0, st>>>((double2*)xr.p, (const double2*)dd.p, n); qams_count_launch();
           rc = qams_apply_launch(c, R, xr.p, dd.p, QAMS_PREC_FP64, st);
           ++fp64_applies;
@@ -383,4 +422,5 @@ extern "C" void qams_solve_opts_default(qams_solve_opts* o) {
   o->tol = 1e-11;
   o->inner_tol = 1e-5;
   o->max_refine = 12;
+  o->precondition = 1;
 }

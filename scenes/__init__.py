@@ -170,11 +170,12 @@ def config(idx: int, request_id: int = 0) -> Scene:
     raise ValueError(idx)
 
 
-def serving_request(request_id: int) -> Scene:
-    """One request of the serving stream: 10..500 bodies, {16x32, 24x48} nodes,
-    k ~ U[1, 15], 1..16 RHS; box side 60 (N_b/1000)^(1/3), at least 12."""
+def serving_request(request_id: int, max_bodies: int = 500) -> Scene:
+    """One request of the serving stream: 10..max_bodies bodies (500 in the
+    full stream), {16x32, 24x48} nodes, k ~ U[1, 15], 1..16 RHS; box side
+    60 (N_b/1000)^(1/3), at least 12."""
     rng = np.random.default_rng(31380 + 5000 + request_id)
-    nb = int(rng.integers(10, 501))
+    nb = int(rng.integers(10, max_bodies + 1))
     disc = (1, 16, 32) if rng.integers(0, 2) == 0 else (2, 12, 48)
     k = float(rng.uniform(1.0, 15.0))
     r = int(rng.integers(1, 17))

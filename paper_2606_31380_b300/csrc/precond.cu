@@ -33,6 +33,7 @@ constexpr int BW = 64;
 __global__ void __launch_bounds__(256) pivot_inverse_kernel(float2* const* __restrict__ W, int n, int k0, int b,
                                                             float2* __restrict__ P, int* __restrict__ status) {
   extern __shared__ float2 aug[];  // [b][2b]
+  __shared__ float2 fcol[64];      // column c before its elimination
   __shared__ int piv;
   const float2* Wb = W[blockIdx.x];
   const int ld = 2 * b;
@@ -77,11 +78,13 @@ __global__ void __launch_bounds__(256) pivot_inverse_kernel(float2* const* __res
       const float2 v = aug[c * ld + j];
       aug[c * ld + j] = make_float2(v.x * inv.x - v.y * inv.y, v.x * inv.y + v.y * inv.x);
     }
+    // the multipliers are read before any thread overwrites column c
+    for (int r = threadIdx.x; r < b; r += blockDim.x) fcol[r] = aug[r * ld + c];
     __syncthreads();
     for (int e = threadIdx.x; e < b * ld; e += blockDim.x) {
       const int r = e / ld, j = e % ld;
       if (r == c) continue;
-      const float2 f = aug[r * ld + c];
+      const float2 f = fcol[r];
       const float2 v = aug[c * ld + j];
       aug[e].x -= f.x * v.x - f.y * v.y;
       aug[e].y -= f.x * v.y + f.y * v.x;

@@ -3,7 +3,9 @@
 
 One step = one full mixed-precision solve of a seeded scene: self-block
 assembly for the wavenumber, incident right-hand sides, GMRES with the FP32
-operator inside FP64 iterative refinement to ||b - A mu|| <= 1e-11 ||b||, and
+operator inside FP64 iterative refinement to ||b - A mu|| <= 1e-10 ||b|| (the
+metric asks for 1e-8 relative error; the error against the FP64 solve is
+reported), and
 the far field on 200 x 200 directions.  Geometry (qams_set_bodies) is
 resident before the timed region; the e2e figure repeats the step through
 the C ABI starting from host descriptors and ending with the densities and
@@ -215,7 +217,7 @@ def run_ours(args, rank, world, local_rank):
         ctx.assemble()
         ev[1].record()
         ctx.incident_plane(sc.directions, b)
-        st = ctx.solve(b, mu, q.PREC_FP32, tol=1e-11)
+        st = ctx.solve(b, mu, q.PREC_FP32, tol=args.tol)
         ev[2].record()
         ctx.farfield(mu, xh, u)
         ev[3].record()
@@ -297,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
         bb = torch.zeros((N, R), dtype=torch.complex128, device="cuda")
         c2.incident_plane(sc.directions, bb)
         mm = torch.zeros_like(bb)
-        st = c2.solve(bb, mm, q.PREC_FP32, tol=1e-11)
+        st = c2.solve(bb, mm, q.PREC_FP32, tol=args.tol)
         uu = torch.zeros((M, R), dtype=torch.complex128, device="cuda")
         c2.farfield(mm, xh, uu)
         mu_h.copy_(mm, non_blocking=True)
@@ -326,7 +328,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32 operator + f64 (assembly, Krylov, refinement)",
         "data": "synthetic (seeded quasi-axisymmetric bodies)",
         "config": {"workload": sc.name, "n_bodies": len(sc.bodies), "N": N, "R": R, "k": sc.k, "eta": sc.eta,
-                   "tol": 1e-11, "far_field_dirs": M, "parallelism": f"replicas x{world}",
+                   "tol": args.tol, "far_field_dirs": M, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (self blocks %.2f GB resident)" % (
                        sum(bd.n_nodes ** 2 for bd in sc.bodies) * 24 / 1e9)},
         "solves_per_s": args.steps * world / elapsed,
@@ -463,6 +465,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bodies", type=int, default=0, help="use only the first B bodies (small profiling case)")
+    ap.add_argument("--tol", type=float, default=1e-10,
+                    help="relative FP64 residual target of the mixed solve (the metric asks 1e-8 relative error)")
     ap.add_argument("--serve", action="store_true", help="serving stream instead of the single-solve step")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-max-bodies", type=int, default=40)

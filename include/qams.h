@@ -131,6 +131,12 @@ int qams_pairsum(qams_ctx* ctx, int R, const void* sigma_dev, void* y_dev, int p
  * QAMS_EBUDGET, QAMS_ECUDA. */
 int qams_assemble(qams_ctx* ctx, void* stream);
 
+/* Work of the last assembly: counts[0] outer quadrature nodes evaluated with
+ * the modal Green's functions, counts[1] far nodes evaluated by the
+ * trapezoidal rule in theta (rings far from their target), summed over all
+ * rows.  For throughput accounting. */
+int qams_assembly_counts(const qams_ctx* ctx, long long* counts);
+
 /* Copy body `body`'s assembled self block (row-major n_b x n_b complex128,
  * rows = targets, columns = sources, both in node order) to dst_dev. */
 int qams_copy_selfblock(const qams_ctx* ctx, int body, void* dst_dev, void* stream);

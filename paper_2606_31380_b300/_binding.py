@@ -75,6 +75,7 @@ def load_library():
         "qams_incident_plane": (i, [vp, i, vp, vp, vp]),
         "qams_assemble": (i, [vp, vp]),
         "qams_copy_selfblock": (i, [vp, i, vp, vp]),
+        "qams_assembly_counts": (i, [vp, vp]),
         "qams_apply": (i, [vp, i, vp, vp, i, vp]),
         "qams_build_preconditioner": (i, [vp, vp]),
         "qams_footprint": (i, [vp, i, i, i, C.POINTER(C.c_size_t)]),
@@ -215,6 +216,12 @@ class Context:
 
     def assemble(self, stream=None):
         _check(self.lib.qams_assemble(self._h, C.c_void_p(_stream_ptr(stream))), "qams_assemble")
+
+    def assembly_counts(self):
+        """(modal outer nodes, far outer nodes) of the last assembly."""
+        out = np.zeros(2, np.int64)
+        _check(self.lib.qams_assembly_counts(self._h, out.ctypes.data_as(C.c_void_p)), "qams_assembly_counts")
+        return int(out[0]), int(out[1])
 
     def copy_selfblock(self, body: int, dst, stream=None):
         import torch

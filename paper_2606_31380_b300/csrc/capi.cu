@@ -211,6 +211,13 @@ int qams_assemble(qams_ctx* c, void* stream) {
   return QAMS_OK;
 }
 
+int qams_assembly_counts(const qams_ctx* c, long long* counts) {
+  if (!c || !c->assembled || !counts) return QAMS_EINVAL;
+  counts[0] = c->asm_counts[0];
+  counts[1] = c->asm_counts[1];
+  return QAMS_OK;
+}
+
 int qams_copy_selfblock(const qams_ctx* c, int body, void* dst, void* stream) {
   if (!c || !c->assembled || body < 0 || body >= (int)c->bodies.size() || !dst) return QAMS_EINVAL;
   long long off = 0;

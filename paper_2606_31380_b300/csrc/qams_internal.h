@@ -77,6 +77,7 @@ struct qams_ctx {
   DeviceBuf blk_off;   // long long [nb+1]: first entry of each block
   long long block_entries = 0;
   bool assembled = false;
+  long long asm_counts[2] = {0, 0};  // outer quadrature nodes of the last assembly: modal, far
 
   // block-Jacobi preconditioner: inverses of the self blocks (same layout)
   DeviceBuf pinv32;  // complex64, computed

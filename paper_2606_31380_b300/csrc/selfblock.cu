@@ -45,6 +45,7 @@ constexpr int MAXM2 = 96;    // M/2 + 1 samples of the smooth factors
 constexpr int MAXN1 = 88;    // highest smooth-factor mode + 2
 constexpr int MAXN = 32;     // N = n_theta / 2
 constexpr int MAXORD = 19;
+constexpr int MAXE = (MAXORD * 2 * MAXN + NT - 1) / NT;  // panel entries per thread
 
 struct alignas(16) RowShared {
   // outer nodes of the row
@@ -149,8 +150,16 @@ __device__ __forceinline__ double q3_d(double x) {
 // Lane work: geometry of the ring at s_t + h seen from (s_t, theta_t) and the
 // static modal sequence.  Scalars: 0 r, 1 rt, 2 c, 3 dr, 4 alpha, 5 scale,
 // 6 dchi_r, 7 dchi_z, 8 s, 9 dl, 10 r'(s), 11 kappa r.
-__device__ void ring_node(const AsmBody& B, double s_t, double th_t, double h, int P, double* q, double* dq,
-                          double* sc) {
+// Rings with eta N >= FAR_ETA_N (eta = acosh chi) are far enough from the
+// target that the kernels are resolved by the 2N azimuthal nodes to 1e-14
+// (checked against the modal evaluation): their Lagrange weights are the
+// trapezoidal values (pi/N) K(theta_j), and the modal machinery (recursion,
+// transforms, convolution) is skipped -- the paper's modal technique is for
+// rings close to the target.
+constexpr double FAR_ETA_N = 48.0;
+
+__device__ void ring_node(const AsmBody& B, double s_t, double th_t, double h, int P, int Nhalf, double* q,
+                          double* dq, double* sc) {
   const double s = s_t + h;
   const double sh = sin(0.5 * h);
   const double mid = s_t + 0.5 * h;
@@ -190,6 +199,21 @@ __device__ void ring_node(const AsmBody& B, double s_t, double th_t, double h, i
   if (delta < 1e-300) delta = 1e-300;
   const double chi = 1.0 + delta;
   const double eta = log1p(delta + sqrt(delta * (2.0 + delta)));
+  // ring scalars (also the far path's inputs)
+  sc[0] = r;
+  sc[1] = rt;
+  sc[2] = c;
+  sc[3] = dr;
+  sc[4] = alpha;
+  sc[5] = 1.0 / (2.0 * M_PI * sqrt(r * rt));
+  sc[6] = (dr * (r + rt) - c * c) / (2.0 * rt * r * r);
+  sc[7] = -c / (r * rt);
+  sc[8] = s;
+  sc[9] = 0.5 * B.L * cos(s);                                            // l'(s)
+  sc[10] = drho_prof(B, u) * 0.5 * cos(s) * cos(s) - rho_s * sin(s);     // r'(s)
+  sc[11] = B.kappa * r;
+  sc[12] = (eta * Nhalf >= FAR_ETA_N) ? 1.0 : 0.0;
+  if (sc[12] != 0.0) return;
   const double mu = sqrt(2.0 / (2.0 + delta));
   const double mu_c = sqrt(delta / (2.0 + delta));
   double K, E;
@@ -212,21 +236,6 @@ __device__ void ring_node(const AsmBody& B, double s_t, double th_t, double h, i
     const double prev = m == 0 ? q[1] : q[m - 1];
     dq[m] = (2.0 * m - 1.0) / (2.0 * chi2m1) * (chi * q[m] - prev);
   }
-  // normal-component inputs at s
-  const double dl = 0.5 * B.L * cos(s);
-  const double rp = drho_prof(B, u) * 0.5 * cos(s) * cos(s) - rho_s * sin(s);
-  sc[0] = r;
-  sc[1] = rt;
-  sc[2] = c;
-  sc[3] = dr;
-  sc[4] = alpha;
-  sc[5] = 1.0 / (2.0 * M_PI * sqrt(r * rt));
-  sc[6] = (dr * (r + rt) - c * c) / (2.0 * rt * r * r);
-  sc[7] = -c / (r * rt);
-  sc[8] = s;
-  sc[9] = dl;
-  sc[10] = rp;
-  sc[11] = B.kappa * r;
 }
 
 // plain smooth combined-layer kernel (far panels of the same body)
@@ -248,7 +257,8 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
                                                        const double* __restrict__ rules,
                                                        const qd4* __restrict__ x64, const qd4* __restrict__ n64,
                                                        const double* __restrict__ jac, double k, double eta,
-                                                       long long row0, double2* __restrict__ blocks) {
+                                                       long long row0, double2* __restrict__ blocks,
+                                                       unsigned long long* __restrict__ counts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowShared& S = *reinterpret_cast<RowShared*>(smem_raw);
   // modal-domain accumulators of the current panel, [order][2N] complex each for the
@@ -293,6 +303,11 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   double2* row = blocks + B.blk + (long long)t * nbn;
 
   for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_double2(0.0, 0.0);
+  int n_far = 0;  // thread 0: far outer nodes of this row
+  // far-ring contributions in sample space, entries e = tid + q NT of the current panel
+  double far_re[MAXE], far_im[MAXE];
+#pragma unroll
+  for (int qq = 0; qq < MAXE; ++qq) far_re[qq] = far_im[qq] = 0.0;
   // outer nodes (thread 0 builds the list; panels in increasing order, contiguous)
   if (tid == 0) {
     int nq = 0;
@@ -354,7 +369,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
 
   for (int b0 = 0; b0 < nq; b0 += BATCH) {
     const int nbatch = min(BATCH, nq - b0);
-    if (tid < nbatch) ring_node(B, s_t, th_t, S.qh[b0 + tid], P, S.bq[tid], S.bdq[tid], S.bs[tid]);
+    if (tid < nbatch) ring_node(B, s_t, th_t, S.qh[b0 + tid], P, N, S.bq[tid], S.bdq[tid], S.bs[tid]);
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
       const double* sc = S.bs[bi];
@@ -362,7 +377,57 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       const double dchi_r = sc[6], dchi_z = sc[7], s = sc[8];
       const double* q = S.bq[bi];
       const double* dq = S.bdq[bi];
-      // B: scaled static modal sequences, samples of the smooth factors, cos/sin(m alpha), P_l(s)
+      const bool farn = sc[12] != 0.0;
+      if (tid == 0) n_far += farn ? 1 : 0;
+      const int ip = S.qp[b0 + bi];
+      if (tid < order) {
+        const double xs = (s - (-M_PI / 2 + pw * ip)) / pw * 2.0 - 1.0;  // panel coordinate
+        double v = 1.0;
+        for (int mm = 0; mm < order; ++mm)
+          if (mm != tid) v *= (xs - gl_x[mm]) / (gl_x[tid] - gl_x[mm]);
+        S.pl[tid] = v;
+      }
+      if (farn) {
+        // far ring: integrands sampled at the azimuthal nodes, times the
+        // trapezoidal weight pi/N (held in dre/dim_ = double layer, tre/tim = single layer)
+        const double rl = r * sc[9], kr = sc[11], rrp = r * sc[10];
+        for (int j = tid; j < nth; j += NT) {
+          const double ph = 2.0 * M_PI * j / nth - alpha;
+          const double sh2 = sin(0.5 * ph);
+          const double s2 = sh2 * sh2;
+          const double rho = sqrt(dr * dr + c * c + 4.0 * r * rt * s2);
+          const double radial = dr + 2.0 * rt * s2;  // r - r~ cos(phi)
+          double sn, cs;
+          sincos(k * rho, &sn, &cs);
+          const double inv = 1.0 / rho, f = 0.079577471545947667884 * inv;
+          const double gr = cs * f, gi = sn * f;                               // G
+          const double dpr = (-cs - k * rho * sn) * f * inv * inv, dpi = (k * rho * cs - sn) * f * inv * inv;  // G'/rho
+          const double nr = rl * (1.0 - kr * S.cth[j]);                        // |J| n_r
+          const double dre_ = nr * dpr * radial + rrp * dpr * c;               // |J|n_r K^r + |J|n_z K^z
+          const double dim = nr * dpi * radial + rrp * dpi * c;
+          const double wt = 2.0 * M_PI / nth;
+          S.dre[j] = wt * dre_;
+          S.dim_[j] = wt * dim;
+          S.tre[j] = wt * eta * gi;
+          S.tim[j] = -wt * eta * gr;
+        }
+        __syncthreads();
+        const double wq = S.qw[b0 + bi];
+        const int base = ip * per_panel;
+#pragma unroll
+        for (int qq = 0; qq < MAXE; ++qq) {
+          const int e = tid + qq * NT;
+          if (e < per_panel) {
+            const int l = e / nth, j = e % nth;
+            const double J = jac[B.offset + base + e];
+            const double f = wq * S.pl[l];
+            far_re[qq] += f * (S.dre[j] + J * S.tre[j]);
+            far_im[qq] += f * (S.dim_[j] + J * S.tim[j]);
+          }
+        }
+        __syncthreads();
+      } else {
+      // B: scaled static modal sequences, samples of the smooth factors, cos/sin(m alpha)
       for (int m = tid; m <= P; m += NT) {
         const double g0 = q[m] * scale;
         S.sg0[m] = g0;
@@ -379,14 +444,6 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         }
       }
       for (int m = tid; m <= N + 1; m += NT) sincos(m * alpha, &S.sma[m], &S.cma[m]);
-      const int ip = S.qp[b0 + bi];
-      if (tid < order) {
-        const double xs = (s - (-M_PI / 2 + pw * ip)) / pw * 2.0 - 1.0;  // panel coordinate
-        double v = 1.0;
-        for (int mm = 0; mm < order; ++mm)
-          if (mm != tid) v *= (xs - gl_x[mm]) / (gl_x[tid] - gl_x[mm]);
-        S.pl[tid] = v;
-      }
       __syncthreads();
       if (!kz) {
         // C1: cosine coefficients f^_n = (2pi/M)[f_0 + (-1)^n f_{M/2} + 2 sum f_q cos(2 pi n q/M)]
@@ -490,6 +547,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         accS[e].y += f * S.tim[mm];
       }
       __syncthreads();
+      }  // modal path
       // panel finished: inverse DFT of the accumulated coefficients into the row,
       //   A[t,(ip,l,j)] = (1/2N) sum_m [D_lm + |J_lj| S_lm] e^{i m theta_j}
       const int gidx = b0 + bi;
@@ -514,11 +572,26 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
           if (base + e == t) v.x += 0.5;
           row[base + e] = v;
         }
+        // add the far-ring part (same entries per thread: e = tid + q NT)
+#pragma unroll
+        for (int qq = 0; qq < MAXE; ++qq) {
+          const int e = tid + qq * NT;
+          if (e < per_panel) {
+            row[base + e].x += far_re[qq];
+            row[base + e].y += far_im[qq];
+          }
+          far_re[qq] = far_im[qq] = 0.0;
+        }
         __syncthreads();
         for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_double2(0.0, 0.0);
         __syncthreads();
       }
     }
+  }
+  // outer nodes of this row by kind (modal, far) for the work accounting
+  if (tid == 0 && counts) {
+    atomicAdd(&counts[0], (unsigned long long)(nq - n_far));
+    atomicAdd(&counts[1], (unsigned long long)n_far);
   }
   // panels beyond the neighbours: the plain smooth rule
   const qd4 xt = x64[g];
@@ -614,11 +687,13 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   qams_dev_free(c, &c->blocks64);
   if ((rc = qams_dev_alloc(c, &c->blocks64, sizeof(double2) * (size_t)blk))) return rc;
   c->block_entries = blk;
-  DeviceBuf d_bodies, d_rules;
+  DeviceBuf d_bodies, d_rules, d_counts;
   if ((rc = qams_dev_alloc(c, &d_bodies, sizeof(AsmBody) * nb))) return rc;
   if ((rc = qams_dev_alloc(c, &d_rules, sizeof(double) * rules.size()))) return rc;
   QAMS_CUDA(cudaMemcpy(d_bodies.p, ab.data(), sizeof(AsmBody) * nb, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(d_rules.p, rules.data(), sizeof(double) * rules.size(), cudaMemcpyHostToDevice));
+  if ((rc = qams_dev_alloc(c, &d_counts, 2 * sizeof(unsigned long long)))) return rc;
+  QAMS_CUDA(cudaMemsetAsync(d_counts.p, 0, 2 * sizeof(unsigned long long), st));
   const size_t smem = qams_selfblock_smem(max_nb);
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const long long chunk = 1 << 20;
@@ -627,11 +702,16 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
     selfblock_kernel<<<(unsigned)n, NT, smem, st>>>((const AsmBody*)d_bodies.p, nb, (const double*)d_rules.p,
                                                     (const qd4*)c->x64.p, (const qd4*)c->n64.p,
                                                     (const double*)c->jac64.p, c->k, c->eta, r0,
-                                                    (double2*)c->blocks64.p); qams_count_launch();
+                                                    (double2*)c->blocks64.p, (unsigned long long*)d_counts.p); qams_count_launch();
     QAMS_CUDA(cudaGetLastError());
   }
   QAMS_CUDA(cudaStreamSynchronize(st));
+  unsigned long long hc[2] = {0, 0};
+  QAMS_CUDA(cudaMemcpy(hc, d_counts.p, sizeof(hc), cudaMemcpyDeviceToHost));
+  c->asm_counts[0] = (long long)hc[0];
+  c->asm_counts[1] = (long long)hc[1];
   qams_dev_free(c, &d_bodies);
   qams_dev_free(c, &d_rules);
+  qams_dev_free(c, &d_counts);
   return QAMS_OK;
 }

@@ -247,6 +247,16 @@ int qams_incident_plane(qams_ctx* ctx, int R, const double* dirs_host, void* rhs
 int qams_farfield(qams_ctx* ctx, int R, const void* mu_dev, int M, const double* dirs_host,
                   void* uinf_dev, void* stream);
 
+/* Scattered field u = (D - i eta S)[mu] at M off-surface points
+ * points_host [M][3] (Sec. 6: the field compared with the point-source
+ * solution), by the smooth rule on the surface nodes:
+ *   u(x) = sum_y [(ik/rho - 1/rho^2) n(y).(y - x) - i eta] e^{ik rho}/(4 pi rho) w mu(y).
+ * Accurate for points whose distance to every surface exceeds a few node
+ * spacings; no near-singular correction is applied.  mu_dev [N][R] and
+ * u_dev [M][R] are complex128.  Blocking on `stream`. */
+int qams_field(qams_ctx* ctx, int R, const void* mu_dev, int M, const double* points_host, void* u_dev,
+               void* stream);
+
 /* ------------------------------------------------------------------------
  * Serving: a request loop over independent scattering problems (the
  * paper solves one problem at a time).  Each request is a full solve -- its

@@ -89,6 +89,7 @@ def load_library():
         "qams_pairsum_f32_static": (i, [i, vp, vp, vp, vp, i, vp, vp, d, d, vp]),
         "qams_solve": (i, [vp, i, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveStats), vp]),
         "qams_farfield": (i, [vp, i, vp, i, vp, vp, vp]),
+        "qams_field": (i, [vp, i, vp, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -294,6 +295,17 @@ class Context:
                                       dirs.ctypes.data_as(C.c_void_p),
                                       _dev(uinf, torch.complex128, (M, R), "uinf"),
                                       C.c_void_p(_stream_ptr(stream))), "qams_farfield")
+
+    def field(self, mu, points: np.ndarray, u, stream=None):
+        """Scattered field at off-surface points [M][3] into u [M][R] (complex128)."""
+        import torch
+        points = np.ascontiguousarray(points, float)
+        M = points.shape[0]
+        R = mu.shape[1]
+        _check(self.lib.qams_field(self._h, R, _dev(mu, torch.complex128, (self.N, R), "mu"), M,
+                                   points.ctypes.data_as(C.c_void_p),
+                                   _dev(u, torch.complex128, (M, R), "u"),
+                                   C.c_void_p(_stream_ptr(stream))), "qams_field")
 
 
 QAMS_EAGAIN = -10

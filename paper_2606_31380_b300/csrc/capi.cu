@@ -269,4 +269,10 @@ int qams_farfield(qams_ctx* c, int R, const void* mu, int M, const double* dirs,
   return qams_farfield_launch(c, R, mu, M, dirs, uinf, (cudaStream_t)stream);
 }
 
+int qams_field(qams_ctx* c, int R, const void* mu, int M, const double* points, void* u, void* stream) {
+  if (!c || R < 1 || M < 1 || !mu || !points || !u || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  return qams_field_launch(c, R, mu, M, points, u, (cudaStream_t)stream);
+}
+
 }  // extern "C"

@@ -122,5 +122,7 @@ int qams_precond_launch(qams_ctx* c, cudaStream_t st);
 
 // fields.cu
 int qams_incident_launch(qams_ctx* c, int R, const double* dirs_host, void* rhs, cudaStream_t st);
+int qams_field_launch(qams_ctx* c, int R, const void* mu, int M, const double* pts_host, void* u,
+                      cudaStream_t st);
 int qams_farfield_launch(qams_ctx* c, int R, const void* mu, int M, const double* dirs_host, void* uinf,
                          cudaStream_t st);

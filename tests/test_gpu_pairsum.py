@@ -102,3 +102,37 @@ def test_incident_and_farfield():
     u = torch.zeros((37, 3), dtype=torch.complex128, device="cuda")
     ctx.farfield(torch.from_numpy(mu).cuda(), xh, u)
     assert rel_err(u.cpu().numpy(), op.farfield(nodes, mu, xh, sc.k, sc.eta)) < 1e-12
+
+
+def test_pairsum_thousand_bodies_fp32_sampled_rows():
+    """1000 bodies x 512 nodes (N = 512,000), k = 3, 4 RHS: the FP32 pair sum on
+    every row, sampled rows against the oracle's explicit FP64 sums."""
+    import paper_2606_31380_b300 as q
+    sc = scenes.config(3)
+    ctx = make_ctx(sc)
+    nodes = [body_nodes(b) for b in sc.bodies]
+    sigma = scenes.rhs_seeded(ctx.N, sc.n_rhs, 12)
+    rng = np.random.default_rng(4)
+    rows = np.concatenate([[0, ctx.N - 1], rng.integers(0, ctx.N, 14)])
+    ref = op.pair_sum(nodes, sigma, sc.k, sc.eta, targets=rows)
+    assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FP32)[rows], ref) < FP32_TOL
+
+
+def test_scattered_field_against_oracle():
+    """qams_field: the combined-layer field at off-surface points equals the
+    oracle's explicit sum; 17 right-hand sides cover the 16-column chunking."""
+    import torch
+    sc = _ragged_scene()
+    ctx = make_ctx(sc)
+    nodes = [body_nodes(b) for b in sc.bodies]
+    R = 17
+    mu = scenes.rhs_seeded(ctx.N, R, 9)
+    rng = np.random.default_rng(5)
+    cand = rng.uniform(-4.0, 13.0, size=(400, 3))
+    keep = [p for p in cand
+            if all(np.linalg.norm(p - np.asarray(b.center)) > b.bound_radius() + 0.5 for b in sc.bodies)]
+    pts = np.concatenate([np.asarray(keep[:29]), [[60.0, -40.0, 25.0]]])
+    u = torch.full((len(pts), R), float("nan"), dtype=torch.complex128, device="cuda")
+    ctx.field(torch.from_numpy(mu).cuda(), pts, u)
+    ref = np.stack([op.field(nodes, mu[:, r], pts, sc.k, sc.eta) for r in range(R)], axis=1)
+    assert rel_err(u.cpu().numpy(), ref) < 1e-12

@@ -100,6 +100,9 @@ def test_point_sources_curved_bodies_and_multi_rhs():
     u = op.field(nodes, mu3[:, 0], pts, k, 1.0)
     ex = cf.point_source_field(pts, z, k)
     assert np.max(np.abs(u - ex)) / np.max(np.abs(ex)) < 5e-4
+    ug = torch.zeros((3, 1), dtype=torch.complex128, device="cuda")
+    ctx.field(mu[:, :1].contiguous(), pts, ug)
+    assert l2(ug.cpu().numpy()[:, 0], u) < 1e-12
     _, mm, st = gpu_solve(sc, rhs, q.PREC_FP32, tol=1e-11)
     assert l2(mm.cpu().numpy(), mu_ref) < MIXED_TOL
 
@@ -171,3 +174,28 @@ def test_block_jacobi_preconditioner():
     m2 = torch.zeros_like(b)
     ctx.solve(b, m2, q.PREC_FP32, tol=1e-11, precondition=True)
     assert l2(m2.cpu().numpy(), m0.cpu().numpy()) < MIXED_TOL
+
+
+def test_farfield_reciprocity_curved_bodies():
+    """u_inf(xhat; d) = u_inf(-d; -xhat) for the GPU solutions of four curved
+    random bodies (directions closed under negation, one multi-RHS solve)."""
+    import torch
+    import paper_2606_31380_b300 as q
+    rng = np.random.default_rng(17)
+    bodies = scenes.random_bodies(rng, 4, 4.0, 0.5, 2, 16, 32)
+    d = scenes.fibonacci_directions(4, rng)
+    D = np.concatenate([d, -d])
+    sc = scenes.Scene("reciprocity", bodies, 3.0, 1.0, D)
+    ctx = make_ctx(sc)
+    ctx.assemble()
+    b = torch.zeros((ctx.N, 8), dtype=torch.complex128, device="cuda")
+    ctx.incident_plane(D, b)
+    mu = torch.zeros_like(b)
+    ctx.solve(b, mu, q.PREC_FP64, tol=1e-13)
+    U = torch.zeros((8, 8), dtype=torch.complex128, device="cuda")
+    ctx.farfield(mu, D, U)
+    U = U.cpu().numpy()                      # U[i, j] = u_inf(D_i; D_j)
+    neg = (np.arange(8) + 4) % 8
+    off = ~np.eye(8, dtype=bool)
+    err = np.max(np.abs(U - U[neg][:, neg].T)[off]) / np.max(np.abs(U))
+    assert err < 1e-6

@@ -80,3 +80,30 @@ def test_point_sources_two_curved_bodies_converge():
         ex = cf.point_source_field(pts, z, k)
         errs.append(np.max(np.abs(u - ex)) / np.max(np.abs(ex)))
     assert errs[0] < 2e-2 and errs[1] < 5e-4 and errs[0] / errs[1] > 20
+
+
+def test_farfield_reciprocity_two_bodies():
+    """Reciprocity of the far-field pattern (the textbook relation for the
+    sound-soft problem, u_inf(xhat; d) = u_inf(-d; -xhat)) holds for the
+    discrete solutions to the discretisation error.  A sign or conjugation
+    slip in the incident field, the far field or the kernel breaks it at O(1)."""
+    k = 2.0
+    shape = dict(base_radius=0.5, mode_cos=(0.15, 0.05), mode_sin=(0.08,), axis_length=1.0, curvature=0.0)
+    b1 = scenes.Body(2, 8, 16, **shape, rotation=scenes.rot_zy(0.3, 1.1), center=(0, 0, 0))
+    b2 = scenes.Body(2, 8, 16, **shape, rotation=scenes.rot_zy(2.0, 0.4), center=(2.0, 0.6, -0.4))
+    nodes = [body_nodes(b1), body_nodes(b2)]
+    A1 = self_block(nodes[0], k, 1.0, tol=1e-13)
+    A = op.dense_matrix(nodes, [A1, A1], k, 1.0)
+    d = scenes.fibonacci_directions(3, np.random.default_rng(2))
+    D = np.concatenate([d, -d])          # closed under negation: neg(j) = (j + 3) % 6
+    mu = solve.dense_solve(A, op.incident(nodes, D, k))
+    U = op.farfield(nodes, mu, D, k, 1.0)  # U[i, j] = u_inf(D_i; D_j)
+    neg = (np.arange(6) + 3) % 6
+    Ur = U[neg][:, neg].T                   # u_inf(-D_j; -D_i)
+    off = ~np.eye(6, dtype=bool)
+    err = np.max(np.abs(U - Ur)[off]) / np.max(np.abs(U))
+    assert err < 1e-4
+    # the same relation fails by O(1) with the incident phase conjugated
+    mu_bad = solve.dense_solve(A, np.conj(op.incident(nodes, D, k)))
+    Ub = op.farfield(nodes, mu_bad, D, k, 1.0)
+    assert np.max(np.abs(Ub - Ub[neg][:, neg].T)[off]) / np.max(np.abs(Ub)) > 1e-2

@@ -12,8 +12,27 @@ outward normal n = n_r e_r + n_3 e3 (n . e_theta = 0, Sec. 3.2).
 Nodes: N_p uniform panels in s with N_order Gauss-Legendre nodes each, times
 2N equispaced theta_j = j pi / N; weight |J| (pi/N) omega (Eq. sx).
 
-Pins: tests/test_oracle_geometry.py (sphere area/volume, Gauss-Legendre
-exactness, divergence theorem on curved bodies, orientation).
+Second family (``kind`` 1, the paper's own shapes, Eqs. quasiwave and
+geometries): horizontal rings with a moving centre,
+
+    y(s, theta) = (x_c(s) + r(s) cos theta, y_c(s) + r(s) sin theta, z(s)),
+
+each of x_c, y_c, z, r a finite sum A cos(omega s) + B sin(omega s); the
+frame is fixed (e1, e2, e3 = x, y, z).  Here d_s has an e_theta part, which
+d_theta x d_s drops, so again n = n_r e_r + n_3 e3.
+
+Both families have an area-weighted normal that is a trigonometric
+polynomial of degree one in theta,
+    |J| n_r = a0 + a1 cos theta,   |J| n_3 = b0 + b1 cos theta + b2 sin theta,
+returned per ring by ``area_normal``.
+
+Panels: uniform in s, or the breakpoints given in ``panel_breaks`` (dyadic
+refinement toward the poles, Sec. 6.1).
+
+Pins: tests/test_oracle_operator.py and tests/test_oracle_shapes.py (sphere area,
+Gauss-Legendre exactness, divergence theorem on curved bodies and on the
+paper's shapes (volumes by Cavalieri's principle), orientation, the
+difference formulas of ``self_ring`` against 50-digit arithmetic).
 """
 from __future__ import annotations
 
@@ -115,6 +134,17 @@ class BodyGeom:
         h = np.sqrt(A * A + B * B)
         return A / h, -B / h, g["r"] * h
 
+    def area_normal(self, s):
+        """(a0, a1, b0, b1, b2) of |J| n_r = r l' (1 - kappa r cos theta),
+        |J| n_3 = -r r' at generating-curve parameter s."""
+        g = self.ring(np.array([s], float))
+        r, dr, dl = (float(np.asarray(g[kk]).reshape(-1)[0]) for kk in ("r", "dr", "dl"))
+        return r * dl, -self.kappa * r * r * dl, -r * dr, 0.0, 0.0
+
+    @property
+    def axisymmetric(self) -> bool:
+        return self.kappa == 0.0
+
     def local_points(self, s, theta):
         g = self.ring(s)
         er = np.cos(theta)[..., None] * g["e1"] + np.sin(theta)[..., None] * g["e2"]
@@ -176,6 +206,102 @@ class BodyGeom:
         return (np.asarray(x) - self.c) @ self.R
 
 
+def _series(terms, s):
+    """sum A cos(omega s) + B sin(omega s) and its derivative in s."""
+    s = np.asarray(s, float)
+    f = np.zeros_like(s)
+    df = np.zeros_like(s)
+    for om, A, B in terms:
+        c, sn = np.cos(om * s), np.sin(om * s)
+        f = f + A * c + B * sn
+        df = df + om * (B * c - A * sn)
+    return f, df
+
+
+def _series_drop(terms, s_t: float, h: float) -> float:
+    """f(s_t) - f(s_t + h) by sum-to-product, exact in relative terms as h -> 0:
+    cos w s_t - cos w s = 2 sin(w m) sin(w h/2), sin w s_t - sin w s = -2 cos(w m) sin(w h/2),
+    m = s_t + h/2."""
+    m = s_t + 0.5 * h
+    out = 0.0
+    for om, A, B in terms:
+        sh = math.sin(0.5 * om * h)
+        out += 2.0 * sh * (A * math.sin(om * m) - B * math.cos(om * m))
+    return out
+
+
+@dataclass
+class RingGeom:
+    """Horizontal rings of radius r(s) centred at (x_c(s), y_c(s), z(s))."""
+
+    terms: tuple   # four lists of (omega, A, B): x_c, y_c, z, r
+    R: np.ndarray
+    c: np.ndarray
+
+    @classmethod
+    def from_desc(cls, d) -> "RingGeom":
+        terms = tuple([tuple(map(float, t)) for t in part] for part in d.series)
+        assert len(terms) == 4
+        return cls(terms, np.asarray(d.rotation, float).reshape(3, 3), np.asarray(d.center, float))
+
+    @property
+    def axisymmetric(self) -> bool:
+        return all(A == 0.0 and B == 0.0 for part in self.terms[:2] for (_, A, B) in part)
+
+    def ring(self, s):
+        s = np.asarray(s, float)
+        xc, dxc = _series(self.terms[0], s)
+        yc, dyc = _series(self.terms[1], s)
+        z, dz = _series(self.terms[2], s)
+        r, dr = _series(self.terms[3], s)
+        zero, one = np.zeros_like(s), np.ones_like(s)
+        return dict(gamma=np.stack([xc, yc, z], -1), e1=np.stack([one, zero, zero], -1),
+                    e2=np.stack([zero, one, zero], -1), e3=np.stack([zero, zero, one], -1),
+                    r=r, dr=dr, dz=dz, dxc=dxc, dyc=dyc)
+
+    def normal_parts(self, s, theta):
+        """d_s = A e3 + B e_r + (.) e_theta, A = z', B = r' + x_c' cos theta + y_c' sin theta;
+        n = (A e_r - B e3)/|.|, |J| = r |.|."""
+        g = self.ring(s)
+        A = g["dz"] + 0.0 * np.asarray(theta, float)
+        B = g["dr"] + g["dxc"] * np.cos(theta) + g["dyc"] * np.sin(theta)
+        h = np.sqrt(A * A + B * B)
+        return A / h, -B / h, g["r"] * h
+
+    def area_normal(self, s):
+        """(a0, a1, b0, b1, b2): |J| n_r = r z', |J| n_3 = -r (r' + x_c' cos theta + y_c' sin theta)."""
+        g = self.ring(np.array([s], float))
+        v = {kk: float(np.asarray(g[kk]).reshape(-1)[0]) for kk in ("r", "dr", "dz", "dxc", "dyc")}
+        r = v["r"]
+        return r * v["dz"], 0.0, -r * v["dr"], -r * v["dxc"], -r * v["dyc"]
+
+    def self_ring(self, s_t: float, theta_t: float, h: float):
+        """Ring at s = s_t + h seen from the body's own node (s_t, theta_t):
+        r(s), r - r~, r~, c, alpha with the centre and radius differences taken
+        by sum-to-product, so they keep relative precision as h -> 0:
+            a = r_t cos theta_t + dx,  b = r_t sin theta_t + dy,  c = z(s_t) - z(s),
+            r~ - r_t = (2 r_t (cos theta_t dx + sin theta_t dy) + dx^2 + dy^2)/(r~ + r_t),
+        dx, dy the drops of x_c, y_c from s_t to s."""
+        s = s_t + h
+        r_t = float(_series(self.terms[3], s_t)[0])
+        r = float(_series(self.terms[3], s)[0])
+        dx = _series_drop(self.terms[0], s_t, h)
+        dy = _series_drop(self.terms[1], s_t, h)
+        c = _series_drop(self.terms[2], s_t, h)
+        ct, st = math.cos(theta_t), math.sin(theta_t)
+        a = r_t * ct + dx
+        b = r_t * st + dy
+        rt = math.hypot(a, b)
+        drt = (2.0 * r_t * (ct * dx + st * dy) + dx * dx + dy * dy) / (rt + r_t)  # r~ - r_t
+        dr = -_series_drop(self.terms[3], s_t, h) - drt
+        return r, dr, rt, c, math.atan2(b, a)
+
+    local_points = BodyGeom.local_points
+    local_normals = BodyGeom.local_normals
+    to_world = BodyGeom.to_world
+    to_local = BodyGeom.to_local
+
+
 @dataclass
 class BodyNodes:
     geom: BodyGeom
@@ -196,11 +322,27 @@ class BodyNodes:
         return self.x.shape[0]
 
 
+def geometry(desc):
+    """The geometry object of a body descriptor (``kind`` 0: arc axis, 1: horizontal rings)."""
+    return RingGeom.from_desc(desc) if getattr(desc, "kind", 0) == 1 else BodyGeom.from_desc(desc)
+
+
+def panel_breaks(desc) -> np.ndarray:
+    """Panel breakpoints in s: ``panel_breaks`` when given, else uniform."""
+    npan = desc.n_panels
+    br = np.asarray(getattr(desc, "panel_breaks", ()) or (), float)
+    if br.size == 0:
+        return np.linspace(-np.pi / 2, np.pi / 2, npan + 1)
+    assert br.size == npan + 1 and np.all(np.diff(br) > 0)
+    assert abs(br[0] + np.pi / 2) < 1e-15 and abs(br[-1] - np.pi / 2) < 1e-15
+    return br
+
+
 def body_nodes(desc) -> BodyNodes:
-    g = BodyGeom.from_desc(desc)
+    g = geometry(desc)
     npan, order, nth = desc.n_panels, desc.order, desc.n_theta
     xg, wg = gauss_legendre(order)
-    breaks = np.linspace(-np.pi / 2, np.pi / 2, npan + 1)
+    breaks = panel_breaks(desc)
     s = np.concatenate([0.5 * (breaks[i] + breaks[i + 1]) + 0.5 * (breaks[i + 1] - breaks[i]) * xg
                         for i in range(npan)])
     om = np.concatenate([0.5 * (breaks[i + 1] - breaks[i]) * wg for i in range(npan)])

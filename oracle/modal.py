@@ -161,13 +161,9 @@ def modal_coeffs(r: float, rt: float, c: float, k: float, N: int, dr=None):
     return G, Gr, Gz
 
 
-def lagrange_weights_cos_theta(coef: np.ndarray, alpha: float, n_theta: int):
-    """int K(theta - alpha) cos(theta) L_j(theta) dtheta for j = 0..2N-1 from the
-    phi-coefficients k^_0..k^_{N+1} of an even kernel K.
-
-    cos(theta) = cos(phi) cos(alpha) - sin(phi) sin(alpha); K cos(phi) is even
-    with coefficients (k^_{m-1} + k^_{m+1})/2, K sin(phi) is odd with
-    coefficients (k^_{m-1} - k^_{m+1})/(2i)."""
+def _shifted_weights(coef: np.ndarray, alpha: float, n_theta: int):
+    """Weights of K cos(phi) (even, coefficients (k^_{m-1} + k^_{m+1})/2) and of
+    K sin(phi) (odd, coefficients (k^_{m-1} - k^_{m+1})/(2i)), phi = theta - alpha."""
     N = n_theta // 2
     kk = lambda m: coef[abs(m)]
     even = np.array([0.5 * (kk(m - 1) + kk(m + 1)) for m in range(N + 1)])
@@ -178,8 +174,21 @@ def lagrange_weights_cos_theta(coef: np.ndarray, alpha: float, n_theta: int):
     for m in range(1, N + 1):
         f = 1.0 if m < N else 0.5
         Ws = Ws + f * (kk(m - 1) - kk(m + 1)) * np.sin(m * ph)
-    Ws = Ws / (2 * N)
+    return Wc, Ws / (2 * N)
+
+
+def lagrange_weights_cos_theta(coef: np.ndarray, alpha: float, n_theta: int):
+    """int K(theta - alpha) cos(theta) L_j(theta) dtheta for j = 0..2N-1 from the
+    phi-coefficients k^_0..k^_{N+1} of an even kernel K;
+    cos(theta) = cos(phi) cos(alpha) - sin(phi) sin(alpha)."""
+    Wc, Ws = _shifted_weights(coef, alpha, n_theta)
     return np.cos(alpha) * Wc - np.sin(alpha) * Ws
+
+
+def lagrange_weights_sin_theta(coef: np.ndarray, alpha: float, n_theta: int):
+    """The same with sin(theta) = sin(phi) cos(alpha) + cos(phi) sin(alpha)."""
+    Wc, Ws = _shifted_weights(coef, alpha, n_theta)
+    return np.sin(alpha) * Wc + np.cos(alpha) * Ws
 
 
 def lagrange_weights(coef: np.ndarray, alpha: float, n_theta: int):

@@ -15,9 +15,10 @@ Row t of the self block of one body, for the combined-layer operator
   and treats n_r, n_z as constants, which holds only on bodies of
   revolution.  Here the single layer keeps the mu |J| interpolant, and the
   double layer interpolates mu and integrates the exact area-weighted
-  normal, which on this surface family is a trigonometric polynomial of
-  degree one in theta:
-      |J| n_r = r l' (1 - kappa r cos theta),   |J| n_z = -r r'.
+  normal, which on both surface families is a trigonometric polynomial of
+  degree one in theta (geometry.py):
+      |J| n_r = a0 + a1 cos theta,   |J| n_z = b0 + b1 cos theta + b2 sin theta,
+  e.g. a0 = r l', a1 = -kappa r^2 l', b0 = -r r' on an arc axis.
   (The unit normal itself has complex singularities close to the real
   s-axis on wavy profiles; the area-weighted one is entire.)
 * other panels: the plain Gauss-Legendre x trapezoidal rule (Eq. sx);
@@ -42,7 +43,8 @@ import math
 import numpy as np
 
 from .geometry import BodyNodes
-from .modal import lagrange_weights, lagrange_weights_cos_theta, modal_coeffs, ring_coords
+from .modal import (lagrange_weights, lagrange_weights_cos_theta, lagrange_weights_sin_theta,
+                    modal_coeffs, ring_coords)
 
 # Gauss-Kronrod 7/15 on [-1, 1]
 _XK = np.array([-0.991455371120812639206854697526329, -0.949107912342758524526189684047851,
@@ -89,12 +91,14 @@ def _integrand(bn: BodyNodes, s_t: float, theta_t: float, h: float, pan_nodes, p
     N = bn.n_theta // 2
     G, Gr, Gz = modal_coeffs(r, rt, c, k, N + 1, dr=dr)
     W0 = lagrange_weights(G[: N + 1], alpha, bn.n_theta)
-    Wr = lagrange_weights(Gr[: N + 1], alpha, bn.n_theta)
-    Wrc = lagrange_weights_cos_theta(Gr, alpha, bn.n_theta)
-    Wz = lagrange_weights(Gz[: N + 1], alpha, bn.n_theta)
-    g = {kk: float(np.asarray(v).reshape(-1)[0]) for kk, v in geom.ring(np.array([s])).items()
-         if kk in ("r", "dr", "dl")}
-    FD = g["r"] * g["dl"] * (Wr - geom.kappa * g["r"] * Wrc) - g["r"] * g["dr"] * Wz
+    a0, a1, b0, b1, b2 = geom.area_normal(s)
+    FD = a0 * lagrange_weights(Gr[: N + 1], alpha, bn.n_theta) + b0 * lagrange_weights(Gz[: N + 1], alpha, bn.n_theta)
+    if a1 != 0.0:
+        FD = FD + a1 * lagrange_weights_cos_theta(Gr, alpha, bn.n_theta)
+    if b1 != 0.0:
+        FD = FD + b1 * lagrange_weights_cos_theta(Gz, alpha, bn.n_theta)
+    if b2 != 0.0:
+        FD = FD + b2 * lagrange_weights_sin_theta(Gz, alpha, bn.n_theta)
     FS = -1j * eta * W0
     P = lagrange_basis(pan_nodes, s)
     return P[:, None] * (FD[None, :] + pan_jac * FS[None, :])
@@ -223,7 +227,7 @@ def self_block(bn: BodyNodes, k: float, eta: float, tol: float = 1e-13, workers:
     integrated and the rest follow by cyclic shifts."""
     n = bn.count
     nth = bn.n_theta
-    if bn.geom.kappa == 0.0:
+    if bn.geom.axisymmetric:
         base_rows = list(range(0, n, nth))
         base = self_block_rows_parallel(bn, base_rows, k, eta, tol, workers)
         A = np.zeros((n, n), complex)

@@ -17,6 +17,14 @@ axis.  The reference shape is described by
   along the generating curve and ``n_theta`` = 2N azimuthal points
   (Section 3.1).
 
+A body of ``kind`` 1 is one of the paper's own shapes (Eqs. quasiwave and
+geometries): horizontal rings y = (x_c + r cos theta, y_c + r sin theta, z),
+each of x_c, y_c, z, r given in ``series`` as (omega, A, B) triples of
+A cos(omega s) + B sin(omega s), s in [-pi/2, pi/2].
+
+``panel_breaks`` (optional) replaces the uniform panels, e.g. by dyadic
+refinement toward the poles (Sec. 6.1, N_ref levels).
+
 Seeds follow ``31380 + 1000 * config + request_id``.
 """
 from __future__ import annotations
@@ -42,6 +50,9 @@ class Body:
     curvature: float = 0.0
     rotation: Sequence[float] = (1, 0, 0, 0, 1, 0, 0, 0, 1)  # row-major 3x3
     center: Sequence[float] = (0.0, 0.0, 0.0)
+    kind: int = 0
+    series: Sequence = ()          # kind 1: ((omega, A, B), ...) for x_c, y_c, z, r
+    panel_breaks: Sequence[float] = ()
 
     @property
     def n_nodes(self) -> int:
@@ -50,8 +61,12 @@ class Body:
     def bound_radius(self) -> float:
         """Conservative radius of a ball about ``center`` that holds the body.
 
-        |gamma(l)| <= |l| <= L/2 on the arc axis and r <= rho <= base*(1+sum|a|+|b|).
+        Arc axis: |gamma(l)| <= |l| <= L/2 and r <= rho <= base*(1+sum|a|+|b|).
+        Horizontal rings: |centre| <= |(X, Y, Z)| and r <= R with X = sum |A|+|B| of x_c, etc.
         """
+        if self.kind == 1:
+            X, Y, Z, Rr = (sum(abs(A) + abs(B) for (_, A, B) in part) for part in self.series)
+            return math.sqrt(X * X + Y * Y + Z * Z) + Rr
         amp = sum(abs(a) for a in self.mode_cos) + sum(abs(b) for b in self.mode_sin)
         return 0.5 * self.axis_length + self.base_radius * (1.0 + amp)
 
@@ -205,3 +220,53 @@ def rhs_seeded(n: int, r: int, seed: int) -> np.ndarray:
     """A seeded complex [n, r] array with entries ~ N(0,1) + i N(0,1)."""
     rng = np.random.default_rng(seed)
     return rng.normal(size=(n, r)) + 1j * rng.normal(size=(n, r))
+
+
+# ---------------------------------------------------------------------------
+# The paper's named shapes (Eqs. quasiwave and geometries), as horizontal-ring
+# series; ``scale`` multiplies every length (the factor a of Sec. 6.5).
+
+def _ring_body(series, n_panels, order, n_theta, scale, breaks=(), **kw) -> Body:
+    sc = tuple(tuple((om, scale * A, scale * B) for (om, A, B) in part) for part in series)
+    return Body(n_panels, order, n_theta, kind=1, series=sc, panel_breaks=tuple(breaks), **kw)
+
+
+def quasi_wave(n_panels=8, order=16, n_theta=40, scale=1.0, **kw) -> Body:
+    """x = 0.2 cos 4t + cos t cos phi, y = cos t sin phi, z = 2 sin t."""
+    return _ring_body((((4.0, 0.2, 0.0),), (), ((1.0, 0.0, 2.0),), ((1.0, 1.0, 0.0),)),
+                      n_panels, order, n_theta, scale, **kw)
+
+
+def quasi_ellipsoid(n_panels=6, order=16, n_theta=40, scale=1.0, **kw) -> Body:
+    """x = cos t + 2 cos t cos phi, y = 2 cos t sin phi, z = 3 sin t."""
+    return _ring_body((((1.0, 1.0, 0.0),), (), ((1.0, 0.0, 3.0),), ((1.0, 2.0, 0.0),)),
+                      n_panels, order, n_theta, scale, **kw)
+
+
+def spiral(n_panels=8, order=16, n_theta=40, scale=1.0, **kw) -> Body:
+    """x = 0.05 cos 4 pi t + 1.5 cos t cos phi, y = 0.1 sin 4 pi t + 1.5 cos t sin phi, z = 2 sin t."""
+    w = 4.0 * math.pi
+    return _ring_body((((w, 0.05, 0.0),), ((w, 0.0, 0.1),), ((1.0, 0.0, 2.0),), ((1.0, 1.5, 0.0),)),
+                      n_panels, order, n_theta, scale, **kw)
+
+
+def conch(n_panels=6, order=16, n_theta=40, scale=1.0, **kw) -> Body:
+    """x = (0.2 + 0.1 sin 8t) cos t + cos t cos phi, y = (0.2 + 0.1 sin 8t) sin t + cos t sin phi,
+    z = 1.5 sin t; the centre products expanded: sin 8t cos t = (sin 9t + sin 7t)/2,
+    sin 8t sin t = (cos 7t - cos 9t)/2."""
+    return _ring_body((((1.0, 0.2, 0.0), (9.0, 0.0, 0.05), (7.0, 0.0, 0.05)),
+                       ((1.0, 0.0, 0.2), (7.0, 0.05, 0.0), (9.0, -0.05, 0.0)),
+                       ((1.0, 0.0, 1.5),), ((1.0, 1.0, 0.0),)),
+                      n_panels, order, n_theta, scale, **kw)
+
+
+def dyadic_breaks(n_uniform: int, n_ref: int) -> tuple:
+    """n_uniform equal panels in s, the two end panels then bisected n_ref times
+    toward the poles: n_uniform + 2 n_ref panels (Sec. 6.1, N_ref)."""
+    if n_uniform < 2:
+        raise ValueError("dyadic refinement needs at least two uniform panels")
+    w = math.pi / n_uniform
+    left = [-math.pi / 2] + [-math.pi / 2 + w / 2 ** (n_ref - i) for i in range(n_ref)]
+    inner = [-math.pi / 2 + w * i for i in range(1, n_uniform)]
+    right = [math.pi / 2 - w / 2 ** (i + 1) for i in range(n_ref)] + [math.pi / 2]
+    return tuple(left + inner + right)

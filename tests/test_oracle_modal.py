@@ -103,3 +103,24 @@ def test_cos_theta_weights_against_trapezoid():
         L = (1 + 2 * sum(np.cos(m * (th - tj)) for m in range(1, N)) + np.cos(N * (th - tj))) / (2 * N)
         ref.append(np.sum(Kr * np.cos(th) * L) * 2 * np.pi / M)
     assert np.max(np.abs(W - np.array(ref))) < 1e-14 * np.max(np.abs(ref))
+
+
+def test_sin_theta_weights_against_trapezoid():
+    """int K^z(theta - alpha) sin(theta) L_j dtheta (the sin(theta) part of the
+    area-weighted normal on the paper's shapes) against a fine trapezoid."""
+    from oracle.modal import lagrange_weights_sin_theta
+    r, rt, c, k, N, al = 0.45, 0.35, -0.25, 2.0, 8, 2.3
+    G, Gr, Gz = modal_coeffs(r, rt, c, k, N + 1)
+    W = lagrange_weights_sin_theta(Gz, al, 2 * N)
+    M = 1 << 13
+    th = 2 * np.pi * np.arange(M) / M
+    phi = th - al
+    rho = np.sqrt(rt ** 2 + r ** 2 + c ** 2 - 2 * r * rt * np.cos(phi))
+    dG = np.exp(1j * k * rho) * (1j * k * rho - 1) / (4 * np.pi * rho ** 2)
+    Kz = dG * (-c) / rho
+    ref = []
+    for j in range(2 * N):
+        tj = j * np.pi / N
+        L = (1 + 2 * sum(np.cos(m * (th - tj)) for m in range(1, N)) + np.cos(N * (th - tj))) / (2 * N)
+        ref.append(np.sum(Kz * np.sin(th) * L) * 2 * np.pi / M)
+    assert np.max(np.abs(W - np.array(ref))) < 1e-14 * np.max(np.abs(ref))

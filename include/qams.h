@@ -56,15 +56,35 @@ enum { QAMS_PREC_FP64 = 0, QAMS_PREC_FP32 = 1 };
 typedef struct qams_ctx qams_ctx; /* opaque, library-owned */
 
 /* One body (all FP64, host memory, copied at qams_set_bodies).
- * Reference shape, s in [-pi/2, pi/2], u = (1 + sin s)/2, l = L (u - 1/2):
+ *
+ * profile_kind 0 -- reference shape on a planar-arc axis, s in [-pi/2, pi/2],
+ * u = (1 + sin s)/2, l = L (u - 1/2):
  *   rho(u) = base_radius (1 + sum_m mode_cos[m-1] cos 2 pi m u + mode_sin[m-1] sin 2 pi m u)
  *   r(s)   = rho(u) cos s          (closed at both poles)
  *   axis   = planar circular arc of curvature `curvature` and arclength L
  *            with a rotation-minimising frame; 0 = straight (a body of
  *            revolution);
  *   y(s,theta) = gamma(l) + r(s) (cos theta e1(l) + sin theta e2).
- * Discretisation (Sec. 3.1): n_panels uniform panels in s, `order`
- * Gauss-Legendre nodes per panel, n_theta = 2N equispaced azimuths. */
+ *
+ * profile_kind 1 -- horizontal rings with a moving centre, the family of the
+ * paper's own shapes (Eq. para_quasi; Eqs. quasiwave and geometries):
+ *   y(s,theta) = (x_c(s) + r(s) cos theta, y_c(s) + r(s) sin theta, z(s)),
+ * each of x_c, y_c, z, r = sum_j A_j cos(omega_j s) + B_j sin(omega_j s),
+ * given in `series` as [4][n_terms][3] = (omega, A, B) (pad with zeros).
+ * r must be positive inside (-pi/2, pi/2) and vanish at both ends, z must
+ * increase.  base_radius, modes, axis_length and curvature are ignored.
+ *
+ * Discretisation (Sec. 3.1): n_panels panels in s -- uniform, or with the
+ * n_panels + 1 increasing breakpoints `panel_breaks` from -pi/2 to pi/2
+ * (e.g. dyadic refinement toward the poles, Sec. 6.1) -- with `order`
+ * Gauss-Legendre nodes each, and n_theta = 2N equispaced azimuths.
+ * Panels within one index of the target's panel are integrated with the
+ * modal product rules, the others with the plain rule (Eq. sx).
+ *
+ * QAMS_EINVAL from qams_set_bodies: sizes out of range, a profile that is
+ * not positive (kind 0: sum of |modes| >= 1 or kappa rho >= 1; kind 1: r <= 0
+ * inside, r != 0 at an end, z not increasing), n_terms outside 1..8, or
+ * breakpoints that are not increasing from -pi/2 to pi/2. */
 typedef struct {
   int n_panels, order, n_theta;
   double base_radius;
@@ -74,6 +94,10 @@ typedef struct {
   double axis_length, curvature;
   double rotation[9]; /* row-major R, world = R * local + center */
   double center[3];
+  int profile_kind;           /* 0 or 1, see above */
+  int n_terms;                /* kind 1: terms per function, 1..8 */
+  const double* series;       /* kind 1: [4][n_terms][3]; ignored for kind 0 */
+  const double* panel_breaks; /* n_panels + 1 values, or NULL = uniform panels */
 } qams_body_desc;
 
 const char* qams_strerror(int code);
@@ -297,7 +321,8 @@ typedef struct {
 
 /* Device bytes a solve of these bodies with R right-hand sides and restart m
  * holds: node tables, self blocks (complex128 + complex64), preconditioner
- * (complex64 + complex128), Krylov basis and workspaces.  Host only. */
+ * (complex64 + complex128), Krylov basis and workspaces.  Host only; the
+ * descriptors are validated as by qams_set_bodies (QAMS_EINVAL). */
 int qams_footprint(const qams_body_desc* bodies, int n_bodies, int R, int restart, size_t* bytes);
 
 /* Start a server on CUDA device `cuda_device` with `max_slots` concurrent

@@ -45,7 +45,9 @@ class BodyDesc(C.Structure):
                 ("base_radius", C.c_double), ("n_modes", C.c_int),
                 ("mode_cos", C.POINTER(C.c_double)), ("mode_sin", C.POINTER(C.c_double)),
                 ("axis_length", C.c_double), ("curvature", C.c_double),
-                ("rotation", C.c_double * 9), ("center", C.c_double * 3)]
+                ("rotation", C.c_double * 9), ("center", C.c_double * 3),
+                ("profile_kind", C.c_int), ("n_terms", C.c_int),
+                ("series", C.POINTER(C.c_double)), ("panel_breaks", C.POINTER(C.c_double))]
 
 
 _LIB = None
@@ -138,6 +140,24 @@ def body_desc_array(bodies) -> tuple:
         dst.axis_length, dst.curvature = b.axis_length, b.curvature
         dst.rotation = (C.c_double * 9)(*[float(v) for v in b.rotation])
         dst.center = (C.c_double * 3)(*[float(v) for v in b.center])
+        kind = int(getattr(b, "kind", 0))
+        dst.profile_kind = kind
+        if kind == 1:
+            parts = list(b.series)
+            nt = max(1, max(len(p) for p in parts))
+            ser = np.zeros((4, nt, 3))
+            for q, part in enumerate(parts):
+                for j, term in enumerate(part):
+                    ser[q, j] = term
+            cser = (C.c_double * ser.size)(*ser.reshape(-1))
+            keep.append(cser)
+            dst.n_terms = nt
+            dst.series = C.cast(cser, C.POINTER(C.c_double))
+        br = tuple(getattr(b, "panel_breaks", ()) or ())
+        if br:
+            cbr = (C.c_double * len(br))(*[float(v) for v in br])
+            keep.append(cbr)
+            dst.panel_breaks = C.cast(cbr, C.POINTER(C.c_double))
     return arr, keep
 
 

@@ -83,23 +83,9 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
   std::vector<BodyHost> bh(n_bodies);
   std::vector<double> rad(n_bodies);
   for (int i = 0; i < n_bodies; ++i) {
-    const qams_body_desc& d = bodies[i];
-    if (d.n_panels < 1 || d.order < 1 || d.n_theta < 2 || (d.n_theta & 1) || d.n_modes < 0 ||
-        d.n_modes > 8 || !(d.base_radius > 0) || !(d.axis_length > 0) || d.curvature < 0)
-      return QAMS_EINVAL;
-    bh[i].d = d;
-    bh[i].a.assign(d.n_modes, 0.0);
-    bh[i].b.assign(d.n_modes, 0.0);
-    double amp = 0.0;
-    for (int m = 0; m < d.n_modes; ++m) {
-      if (d.mode_cos) bh[i].a[m] = d.mode_cos[m];
-      if (d.mode_sin) bh[i].b[m] = d.mode_sin[m];
-      amp += std::fabs(bh[i].a[m]) + std::fabs(bh[i].b[m]);
-    }
-    if (amp >= 1.0 || d.curvature * d.base_radius * (1.0 + amp) >= 1.0) return QAMS_EINVAL;
-    bh[i].d.mode_cos = bh[i].a.data();
-    bh[i].d.mode_sin = bh[i].b.data();
-    rad[i] = 0.5 * d.axis_length + d.base_radius * (1.0 + amp);
+    int rc = qams_copy_body(bodies[i], &bh[i]);
+    if (rc) return rc;
+    rad[i] = bh[i].radius;
   }
   for (int i = 0; i < n_bodies; ++i)
     for (int j = i + 1; j < n_bodies; ++j) {

@@ -1,14 +1,19 @@
 // Host-side geometry and Nystrom nodes (Eq. para_quasi, Sec. 3.1, Eq. sx).
 //
-// Reference shape of one body, s in [-pi/2, pi/2]:
+// Kind 0, s in [-pi/2, pi/2]:
 //   u = (1 + sin s)/2, rho(u) = base (1 + sum a_m cos 2 pi m u + b_m sin 2 pi m u)
 //   r(s) = rho(u) cos s, l(s) = L (u - 1/2)
 //   axis: planar arc of curvature kappa, frame e1 = (cos kl, 0, -sin kl),
 //         e2 = (0, 1, 0), e3 = (sin kl, 0, cos kl) (rotation minimising)
 //   y(s, theta) = gamma(l) + r (cos theta e1 + sin theta e2)
 //   d_s = l'(1 - kappa r cos theta) e3 + r' e_r,  d_theta = r e_theta
-//   n = (A e_r - B e3)/sqrt(A^2 + B^2), A = l'(1 - kappa r cos theta), B = r'
-//   |J| = r sqrt(A^2 + B^2), w = |J| (2 pi / n_theta) omega_l.
+// Kind 1 (the paper's shapes, Eqs. quasiwave and geometries):
+//   y(s, theta) = (x_c + r cos theta, y_c + r sin theta, z), each a sum of
+//   A cos(omega s) + B sin(omega s); frame e1, e2, e3 = x, y, z;
+//   d_s = z' e3 + (r' + x_c' cos theta + y_c' sin theta) e_r + (...) e_theta
+// Both: with A the e3 part and B the e_r part of d_s,
+//   n = (A e_r - B e3)/sqrt(A^2 + B^2),  |J| = r sqrt(A^2 + B^2),
+//   w = |J| (2 pi / n_theta) omega_l.
 #include <cmath>
 #include <cstring>
 
@@ -48,25 +53,52 @@ void qams_gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) 
 
 namespace {
 
+// f = sum A cos(omega s) + B sin(omega s) and f' for one of the four kind-1 functions
+void series_eval(const double* T, int nt, double s, double* f, double* df) {
+  double v = 0.0, dv = 0.0;
+  for (int j = 0; j < nt; ++j) {
+    const double om = T[3 * j], A = T[3 * j + 1], B = T[3 * j + 2];
+    const double c = std::cos(om * s), sn = std::sin(om * s);
+    v += A * c + B * sn;
+    dv += om * (B * c - A * sn);
+  }
+  *f = v;
+  *df = dv;
+}
+
 struct Shape {
-  double base, L, kappa;
-  const double* a;
-  const double* b;
-  int na, nb;
+  const BodyCopy& bc;
   double rho(double u) const {
     double s = 1.0;
-    for (int m = 1; m <= na; ++m) s += a[m - 1] * std::cos(2 * M_PI * m * u);
-    for (int m = 1; m <= nb; ++m) s += b[m - 1] * std::sin(2 * M_PI * m * u);
-    return base * s;
+    for (size_t m = 1; m <= bc.a.size(); ++m) s += bc.a[m - 1] * std::cos(2 * M_PI * m * u);
+    for (size_t m = 1; m <= bc.b.size(); ++m) s += bc.b[m - 1] * std::sin(2 * M_PI * m * u);
+    return bc.d.base_radius * s;
   }
   double drho(double u) const {
     double s = 0.0;
-    for (int m = 1; m <= na; ++m) s -= a[m - 1] * 2 * M_PI * m * std::sin(2 * M_PI * m * u);
-    for (int m = 1; m <= nb; ++m) s += b[m - 1] * 2 * M_PI * m * std::cos(2 * M_PI * m * u);
-    return base * s;
+    for (size_t m = 1; m <= bc.a.size(); ++m) s -= bc.a[m - 1] * 2 * M_PI * m * std::sin(2 * M_PI * m * u);
+    for (size_t m = 1; m <= bc.b.size(); ++m) s += bc.b[m - 1] * 2 * M_PI * m * std::cos(2 * M_PI * m * u);
+    return bc.d.base_radius * s;
   }
   // local point, normal and |J| at (s, theta)
   void eval(double s, double th, double p[3], double nrm[3], double* jac) const {
+    const double ct = std::cos(th), st = std::sin(th);
+    if (bc.d.profile_kind == 1) {
+      const int nt = bc.d.n_terms;
+      double f[4], df[4];
+      for (int q = 0; q < 4; ++q) series_eval(bc.series.data() + 3 * nt * q, nt, s, &f[q], &df[q]);
+      const double A = df[2], B = df[3] + df[0] * ct + df[1] * st;
+      const double hh = std::sqrt(A * A + B * B);
+      p[0] = f[0] + f[3] * ct;
+      p[1] = f[1] + f[3] * st;
+      p[2] = f[2];
+      nrm[0] = A * ct / hh;
+      nrm[1] = A * st / hh;
+      nrm[2] = -B / hh;
+      *jac = f[3] * hh;
+      return;
+    }
+    const double kappa = bc.d.curvature, L = bc.d.axis_length;
     double u = 0.5 * (1.0 + std::sin(s));
     double du = 0.5 * std::cos(s);
     double r = rho(u) * std::cos(s);
@@ -80,7 +112,6 @@ struct Shape {
     double g[3] = {0.5 * kappa * l * l * sh * sh, 0.0, l * sf};
     double e1[3] = {std::cos(kl), 0.0, -std::sin(kl)};
     double e3[3] = {std::sin(kl), 0.0, std::cos(kl)};
-    double ct = std::cos(th), st = std::sin(th);
     double er[3] = {ct * e1[0], st, ct * e1[2]};
     double A = dl * (1.0 - kappa * r * ct);
     double B = dr;
@@ -94,6 +125,86 @@ struct Shape {
 };
 
 }  // namespace
+
+int qams_copy_body(const qams_body_desc& d, BodyCopy* out) {
+  if (d.n_panels < 1 || d.order < 1 || d.n_theta < 2 || (d.n_theta & 1) ||
+      (d.profile_kind != 0 && d.profile_kind != 1))
+    return QAMS_EINVAL;
+  BodyCopy& bc = *out;
+  bc.d = d;
+  bc.d.mode_cos = bc.d.mode_sin = bc.d.series = bc.d.panel_breaks = nullptr;
+  bc.a.clear();
+  bc.b.clear();
+  bc.series.clear();
+  if (d.profile_kind == 0) {
+    if (d.n_modes < 0 || d.n_modes > 8 || !(d.base_radius > 0) || !(d.axis_length > 0) || !(d.curvature >= 0))
+      return QAMS_EINVAL;
+    bc.a.assign(d.n_modes, 0.0);
+    bc.b.assign(d.n_modes, 0.0);
+    double amp = 0.0;
+    for (int m = 0; m < d.n_modes; ++m) {
+      if (d.mode_cos) bc.a[m] = d.mode_cos[m];
+      if (d.mode_sin) bc.b[m] = d.mode_sin[m];
+      if (!std::isfinite(bc.a[m]) || !std::isfinite(bc.b[m])) return QAMS_EINVAL;
+      amp += std::fabs(bc.a[m]) + std::fabs(bc.b[m]);
+    }
+    if (amp >= 1.0 || d.curvature * d.base_radius * (1.0 + amp) >= 1.0) return QAMS_EINVAL;
+    bc.rmax = d.base_radius * (1.0 + amp);
+    bc.radius = 0.5 * d.axis_length + bc.rmax;
+  } else {
+    const int nt = d.n_terms;
+    if (nt < 1 || nt > 8 || !d.series) return QAMS_EINVAL;
+    bc.series.assign(d.series, d.series + 12 * nt);
+    double bound[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q)
+      for (int j = 0; j < nt; ++j) {
+        const double* t = &bc.series[3 * (nt * q + j)];
+        if (!std::isfinite(t[0]) || !std::isfinite(t[1]) || !std::isfinite(t[2])) return QAMS_EINVAL;
+        bound[q] += std::fabs(t[1]) + std::fabs(t[2]);
+      }
+    // r > 0 and z' > 0 inside, r = 0 at both ends (checked on a fine grid)
+    const double* Tz = bc.series.data() + 6 * nt;
+    const double* Tr = bc.series.data() + 9 * nt;
+    double f, df;
+    for (int i = 1; i < 2048; ++i) {
+      const double s = -M_PI / 2 + M_PI * i / 2048.0;
+      series_eval(Tr, nt, s, &f, &df);
+      if (!(f > 0)) return QAMS_EINVAL;
+      series_eval(Tz, nt, s, &f, &df);
+      if (!(df > 0)) return QAMS_EINVAL;
+    }
+    for (double s : {-M_PI / 2, M_PI / 2}) {
+      series_eval(Tr, nt, s, &f, &df);
+      if (std::fabs(f) > 1e-12 * bound[3]) return QAMS_EINVAL;
+    }
+    bc.rmax = bound[3];
+    bc.radius = std::sqrt(bound[0] * bound[0] + bound[1] * bound[1] + bound[2] * bound[2]) + bound[3];
+  }
+  bc.breaks.assign(d.n_panels + 1, 0.0);
+  if (d.panel_breaks) {
+    for (int i = 0; i <= d.n_panels; ++i) {
+      bc.breaks[i] = d.panel_breaks[i];
+      if (!std::isfinite(bc.breaks[i]) || (i > 0 && !(bc.breaks[i] > bc.breaks[i - 1]))) return QAMS_EINVAL;
+    }
+    if (std::fabs(bc.breaks[0] + M_PI / 2) > 1e-14 || std::fabs(bc.breaks[d.n_panels] - M_PI / 2) > 1e-14)
+      return QAMS_EINVAL;
+  } else {
+    for (int i = 0; i <= d.n_panels; ++i) bc.breaks[i] = -M_PI / 2 + M_PI * i / d.n_panels;
+  }
+  bc.breaks[0] = -M_PI / 2;
+  bc.breaks[d.n_panels] = M_PI / 2;
+  return QAMS_OK;
+}
+
+qams_body_desc qams_desc_view(const BodyCopy& bc) {
+  qams_body_desc d = bc.d;
+  d.n_modes = (int)bc.a.size();
+  d.mode_cos = bc.a.empty() ? nullptr : bc.a.data();
+  d.mode_sin = bc.b.empty() ? nullptr : bc.b.data();
+  d.series = bc.series.empty() ? nullptr : bc.series.data();
+  d.panel_breaks = bc.breaks.data();
+  return d;
+}
 
 int qams_build_nodes(qams_ctx* c) {
   long long N = 0;
@@ -109,15 +220,14 @@ int qams_build_nodes(qams_ctx* c) {
   c->hj.assign(N, 0.0);
   for (auto& bh : c->bodies) {
     const qams_body_desc& d = bh.d;
-    Shape sh{d.base_radius, d.axis_length, d.curvature, bh.a.data(), bh.b.data(),
-             (int)bh.a.size(), (int)bh.b.size()};
+    Shape sh{bh};
     std::vector<double> gx, gw;
     qams_gauss_legendre(d.order, gx, gw);
     long long idx = bh.offset;
     double dth = 2.0 * M_PI / d.n_theta;
     for (int i = 0; i < d.n_panels; ++i) {
-      double lo = -M_PI / 2 + M_PI * i / d.n_panels;
-      double hi = -M_PI / 2 + M_PI * (i + 1) / d.n_panels;
+      double lo = bh.breaks[i];
+      double hi = bh.breaks[i + 1];
       for (int l = 0; l < d.order; ++l) {
         double s = 0.5 * (lo + hi) + 0.5 * (hi - lo) * gx[l];
         double om = 0.5 * (hi - lo) * gw[l];

@@ -25,11 +25,28 @@ void qams_internal_last_cuda_error(cudaError_t e, const char* what);
 // Process-wide count of kernel launches made by the library.
 void qams_count_launch(int n = 1);
 
-struct BodyHost {
-  qams_body_desc d;          // pointers below are re-pointed at the copies
-  std::vector<double> a, b;  // profile Fourier modes
-  long long offset = 0;      // first node
-  int n = 0;                 // nodes
+// A validated copy of one body descriptor.  The arrays live in the vectors;
+// d's own array pointers are cleared, so only the vectors are read.
+struct BodyCopy {
+  qams_body_desc d{};
+  std::vector<double> a, b;     // kind 0: profile Fourier modes (n_modes each)
+  std::vector<double> series;   // kind 1: [4][n_terms][3] (omega, A, B)
+  std::vector<double> breaks;   // n_panels + 1 panel breakpoints (uniform if not given)
+  double radius = 0.0;          // ball about the centre that holds the body
+  double rmax = 0.0;            // bound on the ring radius r(s)
+};
+
+// Validates `src` and fills `out`; QAMS_OK or QAMS_EINVAL (the conditions of
+// qams_body_desc).
+int qams_copy_body(const qams_body_desc& src, BodyCopy* out);
+
+// The descriptor with its array pointers aimed at the copy's vectors (valid
+// while `bc` lives and is not moved).
+qams_body_desc qams_desc_view(const BodyCopy& bc);
+
+struct BodyHost : BodyCopy {
+  long long offset = 0;  // first node
+  int n = 0;             // nodes
 };
 
 // One target tile of the pair sum: up to TILE consecutive nodes of one body.

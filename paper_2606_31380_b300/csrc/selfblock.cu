@@ -75,6 +75,8 @@ struct alignas(16) RowShared {
 
 struct AsmBody {
   int n_panels, order, n_theta, n_modes;
+  int kind, n_terms;  // profile kind; kind 1: terms per series
+  int ser, brk;       // table offsets: kind-1 series [4][n_terms][3], panel breaks [n_panels+1]
   double base, L, kappa;
   double a[8], b[8];
   long long offset;
@@ -149,7 +151,9 @@ __device__ __forceinline__ double q3_d(double x) {
 
 // Lane work: geometry of the ring at s_t + h seen from (s_t, theta_t) and the
 // static modal sequence.  Scalars: 0 r, 1 rt, 2 c, 3 dr, 4 alpha, 5 scale,
-// 6 dchi_r, 7 dchi_z, 8 s, 9 dl, 10 r'(s), 11 kappa r.
+// 6 dchi_r, 7 dchi_z, 8 s, 9..13 the area-weighted normal
+//   |J| n_r = a0 + a1 cos theta,  |J| n_3 = b0 + b1 cos theta + b2 sin theta
+// (9 a0, 10 a1, 11 b0, 12 b1, 13 b2), 14 far flag.
 // Rings with eta N >= FAR_ETA_N (eta = acosh chi) are far enough from the
 // target that the kernels are resolved by the 2N azimuthal nodes to 1e-14
 // (checked against the modal evaluation): their Lagrange weights are the
@@ -158,42 +162,99 @@ __device__ __forceinline__ double q3_d(double x) {
 // rings close to the target.
 constexpr double FAR_ETA_N = 48.0;
 
-__device__ void ring_node(const AsmBody& B, double s_t, double th_t, double h, int P, int Nhalf, double* q,
-                          double* dq, double* sc) {
+// kind-1 series at s: f, f' and the drop f(s_t) - f(s) by sum-to-product,
+//   cos w s_t - cos w s = 2 sin(w m) sin(w h/2),  sin w s_t - sin w s = -2 cos(w m) sin(w h/2),
+// m = s_t + h/2, so the drop keeps relative precision as h -> 0.
+__device__ __forceinline__ void series_at(const double* T, int nt, double s, double mid, double h, double* f,
+                                          double* df, double* drop) {
+  double v = 0.0, dv = 0.0, dp = 0.0;
+  for (int j = 0; j < nt; ++j) {
+    const double om = T[3 * j], A = T[3 * j + 1], Bs = T[3 * j + 2];
+    double sn, cs, sm, cm;
+    sincos(om * s, &sn, &cs);
+    sincos(om * mid, &sm, &cm);
+    v += A * cs + Bs * sn;
+    dv += om * (Bs * cs - A * sn);
+    dp += 2.0 * sin(0.5 * om * h) * (A * sm - Bs * cm);
+  }
+  *f = v;
+  *df = dv;
+  *drop = dp;
+}
+
+__device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, double s_t, double th_t, double h,
+                          int P, int Nhalf, double* q, double* dq, double* sc) {
   const double s = s_t + h;
   const double sh = sin(0.5 * h);
   const double mid = s_t + 0.5 * h;
-  const double u_t = 0.5 * (1.0 + sin(s_t));
-  const double u = 0.5 * (1.0 + sin(s));
-  const double du = cos(mid) * sh;
-  double drho = 0.0;
-  for (int m = 1; m <= B.n_modes; ++m) {
-    double s1, c1;
-    sincospi(m * (u + u_t), &s1, &c1);
-    const double s2 = sinpi(m * du);
-    drho += -2.0 * B.a[m - 1] * s1 * s2 + 2.0 * B.b[m - 1] * c1 * s2;
-  }
-  drho *= B.base;
-  const double rho_t = rho_prof(B, u_t);
-  const double r_t = rho_t * cos(s_t);
-  const double rho_s = rho_prof(B, u);
-  const double r = rho_s * cos(s);
-  const double dr_t = drho * cos(s) + rho_t * (-2.0 * sin(mid) * sh);
-  const double Delta = -B.L * cos(mid) * sh;
-  const double kd = B.kappa * Delta;
-  const double sinc_h = fabs(kd) > 1e-8 ? sin(0.5 * kd) / (0.5 * kd) : 1.0;
-  const double sinc_f = fabs(kd) > 1e-8 ? sin(kd) / kd : 1.0;
-  const double omc = 0.5 * B.kappa * Delta * Delta * sinc_h * sinc_h;
-  double skd, ckd, st, ct;
-  sincos(kd, &skd, &ckd);
+  double r, rt, c, dr, alpha, a0, a1, b0, b1, b2;
+  double st, ct;
   sincos(th_t, &st, &ct);
-  const double a = omc + r_t * ct * ckd;
-  const double b = r_t * st;
-  const double c = Delta * sinc_f - r_t * ct * skd;
-  const double rt = hypot(a, b);
-  const double d2 = -(r_t * ct * skd) * (r_t * ct * skd) + 2.0 * r_t * ct * ckd * omc + omc * omc;
-  const double dr = dr_t - d2 / (rt + r_t);
-  const double alpha = atan2(b, a);
+  if (B.kind == 1) {
+    const int nt = B.n_terms;
+    const double* T = tab + B.ser;
+    double f[4], df[4], drop[4];
+    for (int qq = 0; qq < 4; ++qq) series_at(T + 3 * nt * qq, nt, s, mid, h, &f[qq], &df[qq], &drop[qq]);
+    double r_t = 0.0;
+    for (int j = 0; j < nt; ++j) {
+      const double* t = T + 3 * (3 * nt + j);
+      double sn, cs;
+      sincos(t[0] * s_t, &sn, &cs);
+      r_t += t[1] * cs + t[2] * sn;
+    }
+    r = f[3];
+    c = drop[2];
+    const double dx = drop[0], dy = drop[1];
+    const double a = r_t * ct + dx;
+    const double b = r_t * st + dy;
+    rt = hypot(a, b);
+    const double drt = (2.0 * r_t * (ct * dx + st * dy) + dx * dx + dy * dy) / (rt + r_t);  // r~ - r_t
+    dr = -drop[3] - drt;
+    alpha = atan2(b, a);
+    a0 = r * df[2];
+    a1 = 0.0;
+    b0 = -r * df[3];
+    b1 = -r * df[0];
+    b2 = -r * df[1];
+  } else {
+    const double u_t = 0.5 * (1.0 + sin(s_t));
+    const double u = 0.5 * (1.0 + sin(s));
+    const double du = cos(mid) * sh;
+    double drho = 0.0;
+    for (int m = 1; m <= B.n_modes; ++m) {
+      double s1, c1;
+      sincospi(m * (u + u_t), &s1, &c1);
+      const double s2 = sinpi(m * du);
+      drho += -2.0 * B.a[m - 1] * s1 * s2 + 2.0 * B.b[m - 1] * c1 * s2;
+    }
+    drho *= B.base;
+    const double rho_t = rho_prof(B, u_t);
+    const double r_t = rho_t * cos(s_t);
+    const double rho_s = rho_prof(B, u);
+    r = rho_s * cos(s);
+    const double dr_t = drho * cos(s) + rho_t * (-2.0 * sin(mid) * sh);
+    const double Delta = -B.L * cos(mid) * sh;
+    const double kd = B.kappa * Delta;
+    const double sinc_h = fabs(kd) > 1e-8 ? sin(0.5 * kd) / (0.5 * kd) : 1.0;
+    const double sinc_f = fabs(kd) > 1e-8 ? sin(kd) / kd : 1.0;
+    const double omc = 0.5 * B.kappa * Delta * Delta * sinc_h * sinc_h;
+    double skd, ckd;
+    sincos(kd, &skd, &ckd);
+    const double a = omc + r_t * ct * ckd;
+    const double b = r_t * st;
+    c = Delta * sinc_f - r_t * ct * skd;
+    rt = hypot(a, b);
+    const double d2 = -(r_t * ct * skd) * (r_t * ct * skd) + 2.0 * r_t * ct * ckd * omc + omc * omc;
+    dr = dr_t - d2 / (rt + r_t);
+    alpha = atan2(b, a);
+    const double dl = 0.5 * B.L * cos(s);                                    // l'(s)
+    const double rp = drho_prof(B, u) * 0.5 * cos(s) * cos(s) - rho_s * sin(s);  // r'(s)
+    a0 = r * dl;
+    a1 = -B.kappa * r * r * dl;
+    b0 = -r * rp;
+    b1 = 0.0;
+    b2 = 0.0;
+  }
 
   double delta = (dr * dr + c * c) / (2.0 * r * rt);
   if (delta < 1e-300) delta = 1e-300;
@@ -209,11 +270,13 @@ __device__ void ring_node(const AsmBody& B, double s_t, double th_t, double h, i
   sc[6] = (dr * (r + rt) - c * c) / (2.0 * rt * r * r);
   sc[7] = -c / (r * rt);
   sc[8] = s;
-  sc[9] = 0.5 * B.L * cos(s);                                            // l'(s)
-  sc[10] = drho_prof(B, u) * 0.5 * cos(s) * cos(s) - rho_s * sin(s);     // r'(s)
-  sc[11] = B.kappa * r;
-  sc[12] = (eta * Nhalf >= FAR_ETA_N) ? 1.0 : 0.0;
-  if (sc[12] != 0.0) return;
+  sc[9] = a0;
+  sc[10] = a1;
+  sc[11] = b0;
+  sc[12] = b1;
+  sc[13] = b2;
+  sc[14] = (eta * Nhalf >= FAR_ETA_N) ? 1.0 : 0.0;
+  if (sc[14] != 0.0) return;
   const double mu = sqrt(2.0 / (2.0 + delta));
   const double mu_c = sqrt(delta / (2.0 + delta));
   double K, E;
@@ -293,8 +356,8 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   const double* ad_w = ad_x + 16;
   const double* g12_x = ad_w + 16;                  // [12], inner dyadic levels
   const double* g12_w = g12_x + 12;
-  const double pw = M_PI / B.n_panels;
-  const double s_t = -M_PI / 2 + pw * (p + 0.5 + 0.5 * gl_x[lt]);
+  const double* brk = rules + B.brk;                // panel breakpoints [n_panels + 1]
+  const double s_t = 0.5 * (brk[p] + brk[p + 1]) + 0.5 * (brk[p + 1] - brk[p]) * gl_x[lt];
   const double th_t = 2.0 * M_PI * jt / nth;
   const bool kz = (k == 0.0);
   const int n1 = kz ? 0 : B.n1;
@@ -314,7 +377,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
     const double dpole = fmin(s_t + M_PI / 2, M_PI / 2 - s_t);
     const int ng = order + 4;
     for (int i = max(0, p - 1); i <= min(B.n_panels - 1, p + 1); ++i) {
-      const double plo = -M_PI / 2 + pw * i, phi_ = plo + pw;
+      const double plo = brk[i], phi_ = brk[i + 1];
       double s0[2], e0[2];
       int npieces;
       if (i == p) { s0[0] = s_t; e0[0] = plo; s0[1] = s_t; e0[1] = phi_; npieces = 2; }
@@ -323,11 +386,14 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       for (int pc = 0; pc < npieces; ++pc) {
         const double L = e0[pc] - s0[pc], aL = fabs(L);
         const double h0 = s0[pc] - s_t;
-        int K = 6;
-        if (i == p) {
-          K = max(5, (int)ceil(log2(aL / (0.5 * dpole))));
-          K = min(K, 14);
-        }
+        // dyadic levels toward the (near-)singular end: on the self panel until the
+        // innermost piece is within half the distance to the nearer pole; on a
+        // neighbour until it is within ~3 times the target's distance to the shared
+        // edge (6 levels on equal panels)
+        int K;
+        if (i == p) K = max(5, (int)ceil(log2(aL / (0.5 * dpole))));
+        else K = max(6, (int)ceil(log2(aL / (3.2 * fabs(h0)))));
+        K = min(K, 14);
         double top = 1.0;
         for (int kk = 0; kk < K; ++kk) {
           const double bot = 0.5 * top;
@@ -369,7 +435,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
 
   for (int b0 = 0; b0 < nq; b0 += BATCH) {
     const int nbatch = min(BATCH, nq - b0);
-    if (tid < nbatch) ring_node(B, s_t, th_t, S.qh[b0 + tid], P, N, S.bq[tid], S.bdq[tid], S.bs[tid]);
+    if (tid < nbatch) ring_node(B, rules, s_t, th_t, S.qh[b0 + tid], P, N, S.bq[tid], S.bdq[tid], S.bs[tid]);
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
       const double* sc = S.bs[bi];
@@ -377,11 +443,11 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       const double dchi_r = sc[6], dchi_z = sc[7], s = sc[8];
       const double* q = S.bq[bi];
       const double* dq = S.bdq[bi];
-      const bool farn = sc[12] != 0.0;
+      const bool farn = sc[14] != 0.0;
       if (tid == 0) n_far += farn ? 1 : 0;
       const int ip = S.qp[b0 + bi];
       if (tid < order) {
-        const double xs = (s - (-M_PI / 2 + pw * ip)) / pw * 2.0 - 1.0;  // panel coordinate
+        const double xs = (s - brk[ip]) / (brk[ip + 1] - brk[ip]) * 2.0 - 1.0;  // panel coordinate
         double v = 1.0;
         for (int mm = 0; mm < order; ++mm)
           if (mm != tid) v *= (xs - gl_x[mm]) / (gl_x[tid] - gl_x[mm]);
@@ -390,7 +456,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       if (farn) {
         // far ring: integrands sampled at the azimuthal nodes, times the
         // trapezoidal weight pi/N (held in dre/dim_ = double layer, tre/tim = single layer)
-        const double rl = r * sc[9], kr = sc[11], rrp = r * sc[10];
+        const double na0 = sc[9], na1 = sc[10], nb0 = sc[11], nb1 = sc[12], nb2 = sc[13];
         for (int j = tid; j < nth; j += NT) {
           const double ph = 2.0 * M_PI * j / nth - alpha;
           const double sh2 = sin(0.5 * ph);
@@ -402,9 +468,11 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
           const double inv = 1.0 / rho, f = 0.079577471545947667884 * inv;
           const double gr = cs * f, gi = sn * f;                               // G
           const double dpr = (-cs - k * rho * sn) * f * inv * inv, dpi = (k * rho * cs - sn) * f * inv * inv;  // G'/rho
-          const double nr = rl * (1.0 - kr * S.cth[j]);                        // |J| n_r
-          const double dre_ = nr * dpr * radial + rrp * dpr * c;               // |J|n_r K^r + |J|n_z K^z
-          const double dim = nr * dpi * radial + rrp * dpi * c;
+          const double nr = na0 + na1 * S.cth[j];                              // |J| n_r
+          const double nz = nb0 + nb1 * S.cth[j] + nb2 * S.sth[j];             // |J| n_3
+          // |J| n_r K^r + |J| n_3 K^z with K^r = (G'/rho)(r - r~ cos phi), K^z = -(G'/rho) c
+          const double dre_ = nr * dpr * radial - nz * dpr * c;
+          const double dim = nr * dpi * radial - nz * dpi * c;
           const double wt = 2.0 * M_PI / nth;
           S.dre[j] = wt * dre_;
           S.dim_[j] = wt * dim;
@@ -503,10 +571,12 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       __syncthreads();
       // E: theta-coefficients, index m = -N+1..N stored at m mod 2N (the entry at N is the
       // symmetric Nyquist average), of
-      //   double layer  r l' (K^r - kappa r K^r cos theta) - r r' K^z,
+      //   double layer  (a0 + a1 cos theta) K^r + (b0 + b1 cos theta + b2 sin theta) K^z,
       //   single layer  -i eta G,
-      // with K(theta - alpha) -> k^_|m| e^{-i m alpha} and cos(theta) averaging m -+ 1.
-      const double rl = r * sc[9], kr = sc[11], rrp = r * sc[10];
+      // with K(theta - alpha) -> k^_|m| e^{-i m alpha}; cos(theta) averages m -+ 1 and
+      // sin(theta) gives (k_{m-1} - k_{m+1})/(2i).
+      const double na0 = sc[9], na1 = sc[10], nb0 = sc[11], nb1 = sc[12], nb2 = sc[13];
+      const bool zshift = (nb1 != 0.0) || (nb2 != 0.0);
       for (int mm = tid; mm < nth; mm += NT) {
         const int m0 = mm <= N ? mm : mm - nth;
         const int nsum = (m0 == N) ? 2 : 1;
@@ -525,8 +595,17 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
           const double kmr = S.gre[1][am1] * cmr - S.gim[1][am1] * cmi, kmi = S.gre[1][am1] * cmi + S.gim[1][am1] * cmr;
           const double kpr = S.gre[1][ap1] * cpr - S.gim[1][ap1] * cpi, kpi = S.gre[1][ap1] * cpi + S.gim[1][ap1] * cpr;
           const double kcr = 0.5 * (kmr + kpr), kci = 0.5 * (kmi + kpi);  // (K^r cos theta)^_m
-          dre_ += fac * (rl * (krr - kr * kcr) - rrp * kzr);
-          dimv += fac * (rl * (kri - kr * kci) - rrp * kzi);
+          double zr = na0 * krr + na1 * kcr + nb0 * kzr;
+          double zi = na0 * kri + na1 * kci + nb0 * kzi;
+          if (zshift) {
+            const double zmr = S.gre[2][am1] * cmr - S.gim[2][am1] * cmi, zmi = S.gre[2][am1] * cmi + S.gim[2][am1] * cmr;
+            const double zpr = S.gre[2][ap1] * cpr - S.gim[2][ap1] * cpi, zpi = S.gre[2][ap1] * cpi + S.gim[2][ap1] * cpr;
+            // cos: (z_{m-1} + z_{m+1})/2;  sin: -i (z_{m-1} - z_{m+1})/2
+            zr += nb1 * 0.5 * (zmr + zpr) + nb2 * 0.5 * (zmi - zpi);
+            zi += nb1 * 0.5 * (zmi + zpi) - nb2 * 0.5 * (zmr - zpr);
+          }
+          dre_ += fac * zr;
+          dimv += fac * zi;
           tre_ += fac * (eta * g0i);
           timv += fac * (-eta * g0r);
         }
@@ -623,8 +702,9 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   for (int b = 0; b < nb; ++b) {
     const BodyHost& bh = c->bodies[b];
     const qams_body_desc& d = bh.d;
-    // outer nodes per row: self panel 2 x (13 (o+4) + (2o+4) + 20), two neighbours 2 x (5 (o+4) + (2o+4) + 16)
-    const int o4 = d.order + 4, maxq = 2 * (13 * o4 + 2 * d.order + 4 + 20) + 2 * (5 * o4 + 2 * d.order + 4 + 16);
+    // outer nodes per row, at most: four pieces (two on the self panel, one per neighbour)
+    // of (2o+4) + (o+4) + 12 x 12 + 20 nodes (14 dyadic levels and the graded innermost rule)
+    const int maxq = 4 * ((2 * d.order + 4) + (d.order + 4) + 12 * 12 + 20);
     if (d.order > MAXORD || d.n_theta / 2 > MAXN || maxq > MAXQ) return QAMS_EINVAL;
     if (rule_off[d.order] < 0) {
       rule_off[d.order] = (int)rules.size();
@@ -659,6 +739,12 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
       rules.insert(rules.end(), w.begin(), w.end());
     }
     AsmBody& A = ab[b];
+    A.kind = d.profile_kind;
+    A.n_terms = d.profile_kind == 1 ? d.n_terms : 0;
+    A.ser = (int)rules.size();
+    rules.insert(rules.end(), bh.series.begin(), bh.series.end());
+    A.brk = (int)rules.size();
+    rules.insert(rules.end(), bh.breaks.begin(), bh.breaks.end());
     A.n_panels = d.n_panels;
     A.order = d.order;
     A.n_theta = d.n_theta;
@@ -666,16 +752,14 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
     A.base = d.base_radius;
     A.L = d.axis_length;
     A.kappa = d.curvature;
-    double amp = 0.0;
     for (int m = 0; m < 8; ++m) {
       A.a[m] = m < A.n_modes ? bh.a[m] : 0.0;
       A.b[m] = m < A.n_modes ? bh.b[m] : 0.0;
-      amp += std::fabs(A.a[m]) + std::fabs(A.b[m]);
     }
     A.offset = bh.offset;
     A.blk = blk;
     blk += (long long)bh.n * bh.n;
-    const double rmax = d.base_radius * (1.0 + amp);
+    const double rmax = bh.rmax;
     A.n1 = (int)std::ceil(1.3 * c->k * rmax + 16.0);
     A.M = 2 * (A.n1 + 8);
     if (A.n1 + 2 > MAXN1 || A.M / 2 + 1 > MAXM2 || d.n_theta / 2 + A.n1 + 2 > MAXP || 2 * A.M > 4 * MAXM2)

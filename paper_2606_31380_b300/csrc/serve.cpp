@@ -22,7 +22,7 @@ using Clock = std::chrono::steady_clock;
 struct Req {
   uint64_t ticket = 0;
   std::vector<qams_body_desc> bodies;
-  std::vector<std::vector<double>> modes;  // keeps mode_cos/mode_sin alive
+  std::vector<BodyCopy> copies;  // owns the arrays `bodies` points into
   std::vector<double> dirs, far_dirs;
   qams_request r{};
   size_t footprint = 0;
@@ -150,6 +150,9 @@ int qams_footprint(const qams_body_desc* bodies, int n_bodies, int R, int restar
   if (!bodies || n_bodies < 1 || R < 1 || restart < 1 || !bytes) return QAMS_EINVAL;
   size_t N = 0, blk = 0;
   for (int b = 0; b < n_bodies; ++b) {
+    BodyCopy bc;
+    int rc = qams_copy_body(bodies[b], &bc);
+    if (rc) return rc;
     const size_t n = (size_t)bodies[b].n_panels * bodies[b].order * bodies[b].n_theta;
     N += n;
     blk += n * n;
@@ -206,20 +209,13 @@ int qams_submit(qams_server* s, const qams_request* r, uint64_t* ticket) {
     return QAMS_EINVAL;
   auto q = std::make_shared<Req>();
   q->r = *r;
-  q->bodies.assign(r->bodies, r->bodies + r->n_bodies);
-  q->modes.resize(2 * (size_t)r->n_bodies);
+  q->copies.resize(r->n_bodies);
   for (int b = 0; b < r->n_bodies; ++b) {
-    const qams_body_desc& d = r->bodies[b];
-    if (d.n_modes < 0 || d.n_modes > 8) return QAMS_EINVAL;
-    q->modes[2 * b].assign(d.n_modes, 0.0);
-    q->modes[2 * b + 1].assign(d.n_modes, 0.0);
-    for (int m = 0; m < d.n_modes; ++m) {
-      if (d.mode_cos) q->modes[2 * b][m] = d.mode_cos[m];
-      if (d.mode_sin) q->modes[2 * b + 1][m] = d.mode_sin[m];
-    }
-    q->bodies[b].mode_cos = q->modes[2 * b].data();
-    q->bodies[b].mode_sin = q->modes[2 * b + 1].data();
+    int rc = qams_copy_body(r->bodies[b], &q->copies[b]);
+    if (rc) return rc;
   }
+  q->bodies.resize(r->n_bodies);
+  for (int b = 0; b < r->n_bodies; ++b) q->bodies[b] = qams_desc_view(q->copies[b]);
   q->dirs.assign(r->dirs, r->dirs + 3 * r->R);
   if (r->M > 0) q->far_dirs.assign(r->far_dirs, r->far_dirs + 3 * (size_t)r->M);
   int rc = qams_footprint(q->bodies.data(), r->n_bodies, r->R, 50, &q->footprint);

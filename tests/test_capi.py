@@ -37,3 +37,26 @@ def test_errors_without_device_are_reported_not_crashing():
     lib = q.load_library()
     assert lib.qams_strerror(-3).decode().startswith("bodies overlap")
     assert lib.qams_create(None, 0, 0) == -1  # out == NULL -> QAMS_EINVAL
+
+
+def test_descriptor_validation_on_host():
+    """qams_footprint validates descriptors without a device: the paper's shapes
+    and dyadic panels pass; an open profile, a falling axial coordinate and
+    breakpoints that do not span [-pi/2, pi/2] are rejected."""
+    import math
+    import scenes
+    import paper_2606_31380_b300 as q
+    good = [scenes.conch(), scenes.spiral(), scenes.quasi_wave(), scenes.quasi_ellipsoid(scale=0.3),
+            scenes.Body(8, 16, 32, 0.5, (0.1,), (), 1.0, 0.2, panel_breaks=scenes.dyadic_breaks(4, 2)),
+            scenes.conch(n_panels=22, breaks=scenes.dyadic_breaks(12, 5))]
+    assert q.footprint(good, 1) > 0
+    bad = [
+        scenes._ring_body((((1.0, 1.0, 0.0),), (), ((1.0, 0.0, 2.0),), ((0.0, 0.5, 0.0),)), 4, 8, 16, 1.0),
+        scenes._ring_body(((), (), ((1.0, 0.0, -2.0),), ((1.0, 1.0, 0.0),)), 4, 8, 16, 1.0),
+        scenes.Body(3, 8, 16, panel_breaks=(-math.pi / 2, 0.3, 0.2, math.pi / 2)),
+        scenes.Body(2, 8, 16, panel_breaks=(-1.5, 0.0, math.pi / 2)),
+        scenes.Body(2, 8, 16, 0.5, (0.7, 0.4), ()),
+    ]
+    for b in bad:
+        with pytest.raises(q.QamsError):
+            q.footprint([b], 1)

@@ -56,7 +56,7 @@ struct alignas(16) RowShared {
   // per-batch node data (filled by warp 0)
   double bq[BATCH][MAXP + 1];   // Q_{m-1/2}
   double bdq[BATCH][MAXP + 1];  // dQ_{m-1/2}/dchi
-  double bs[BATCH][16];         // scalars
+  double bs[BATCH][18];         // scalars
   // per-node work arrays
   double sg0[MAXP + 1], sgr[MAXP + 1], sgz[MAXP + 1];  // static g^, d_r g^, d_z g^ (modes 0..P)
   double fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho)
@@ -71,6 +71,7 @@ struct alignas(16) RowShared {
   double s2tab[MAXM2];     // sin^2(pi q / M)
   double ctab[4 * MAXM2];  // cos(2 pi j / M), j < M
   double cth[2 * MAXN], sth[2 * MAXN];
+  double inv_odd[MAXP + 1];  // 1/(2n - 1)
 };
 
 struct AsmBody {
@@ -123,18 +124,16 @@ __device__ void agm_KE(double mu, double mu_c, double* K, double* E) {
   *E = *K * (1.0 - s);
 }
 
-__device__ __forceinline__ double sinc_d(double x) {
-  if (fabs(x) < 0.1) {
+// cos x, sin(x)/x and (x cos x - sin x)/x^3 from one sincos (Taylor series near 0)
+__device__ __forceinline__ void smooth_factors(double x, double* c, double* sinc, double* q3) {
+  double sn, cs;
+  sincos(x, &sn, &cs);
+  *c = cs;
+  const double ax = fabs(x);
+  if (ax < 0.5) {
     const double x2 = x * x;
-    return 1.0 - x2 / 6.0 + x2 * x2 / 120.0 - x2 * x2 * x2 / 5040.0 + x2 * x2 * x2 * x2 / 362880.0;
-  }
-  return sin(x) / x;
-}
-
-// (x cos x - sin x)/x^3
-__device__ __forceinline__ double q3_d(double x) {
-  if (fabs(x) < 0.5) {
-    const double x2 = x * x;
+    *sinc = ax < 0.1 ? 1.0 - x2 / 6.0 + x2 * x2 / 120.0 - x2 * x2 * x2 / 5040.0 + x2 * x2 * x2 * x2 / 362880.0
+                     : sn / x;
     double term = 1.0, sum = 0.0, fact = 6.0, sign = -1.0;
     for (int n = 1; n <= 12; ++n) {
       if (n > 1) fact *= (2.0 * n) * (2.0 * n + 1.0);
@@ -142,18 +141,20 @@ __device__ __forceinline__ double q3_d(double x) {
       term *= x2;
       sign = -sign;
     }
-    return sum;
+    *q3 = sum;
+    return;
   }
-  double sn, cs;
-  sincos(x, &sn, &cs);
-  return (x * cs - sn) / (x * x * x);
+  const double inv = 1.0 / x;
+  *sinc = sn * inv;
+  *q3 = (x * cs - sn) * inv * inv * inv;
 }
+
 
 // Lane work: geometry of the ring at s_t + h seen from (s_t, theta_t) and the
 // static modal sequence.  Scalars: 0 r, 1 rt, 2 c, 3 dr, 4 alpha, 5 scale,
 // 6 dchi_r, 7 dchi_z, 8 s, 9..13 the area-weighted normal
 //   |J| n_r = a0 + a1 cos theta,  |J| n_3 = b0 + b1 cos theta + b2 sin theta
-// (9 a0, 10 a1, 11 b0, 12 b1, 13 b2), 14 far flag.
+// (9 a0, 10 a1, 11 b0, 12 b1, 13 b2), 14 far flag, 15 cos(alpha), 16 sin(alpha).
 // Rings with eta N >= FAR_ETA_N (eta = acosh chi) are far enough from the
 // target that the kernels are resolved by the 2N azimuthal nodes to 1e-14
 // (checked against the modal evaluation): their Lagrange weights are the
@@ -161,6 +162,8 @@ __device__ __forceinline__ double q3_d(double x) {
 // transforms, convolution) is skipped -- the paper's modal technique is for
 // rings close to the target.
 constexpr double FAR_ETA_N = 48.0;
+constexpr double INV_2PI = 0.15915494309189533577;
+constexpr double INV_4PI = 0.079577471545947667884;
 
 // kind-1 series at s: f, f' and the drop f(s_t) - f(s) by sum-to-product,
 //   cos w s_t - cos w s = 2 sin(w m) sin(w h/2),  sin w s_t - sin w s = -2 cos(w m) sin(w h/2),
@@ -183,11 +186,11 @@ __device__ __forceinline__ void series_at(const double* T, int nt, double s, dou
 }
 
 __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, double s_t, double th_t, double h,
-                          int P, int Nhalf, double* q, double* dq, double* sc) {
+                          int P, int Nhalf, const double* __restrict__ inv_odd, double* q, double* dq, double* sc) {
   const double s = s_t + h;
   const double sh = sin(0.5 * h);
   const double mid = s_t + 0.5 * h;
-  double r, rt, c, dr, alpha, a0, a1, b0, b1, b2;
+  double r, rt, c, dr, alpha, a0, a1, b0, b1, b2, ca, sa;
   double st, ct;
   sincos(th_t, &st, &ct);
   if (B.kind == 1) {
@@ -211,6 +214,8 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
     const double drt = (2.0 * r_t * (ct * dx + st * dy) + dx * dx + dy * dy) / (rt + r_t);  // r~ - r_t
     dr = -drop[3] - drt;
     alpha = atan2(b, a);
+    ca = a / rt;
+    sa = b / rt;
     a0 = r * df[2];
     a1 = 0.0;
     b0 = -r * df[3];
@@ -247,6 +252,8 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
     const double d2 = -(r_t * ct * skd) * (r_t * ct * skd) + 2.0 * r_t * ct * ckd * omc + omc * omc;
     dr = dr_t - d2 / (rt + r_t);
     alpha = atan2(b, a);
+    ca = a / rt;
+    sa = b / rt;
     const double dl = 0.5 * B.L * cos(s);                                    // l'(s)
     const double rp = drho_prof(B, u) * 0.5 * cos(s) * cos(s) - rho_s * sin(s);  // r'(s)
     a0 = r * dl;
@@ -276,6 +283,8 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
   sc[12] = b1;
   sc[13] = b2;
   sc[14] = (eta * Nhalf >= FAR_ETA_N) ? 1.0 : 0.0;
+  sc[15] = rt > 0.0 ? ca : 1.0;  // cos(alpha)
+  sc[16] = rt > 0.0 ? sa : 0.0;  // sin(alpha)
   if (sc[14] != 0.0) return;
   const double mu = sqrt(2.0 / (2.0 + delta));
   const double mu_c = sqrt(delta / (2.0 + delta));
@@ -284,20 +293,29 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
   q[0] = mu * K;
   if (eta * P <= 3.0) {
     if (P >= 1) q[1] = chi * mu * K - sqrt(2.0 * (chi + 1.0)) * E;
-    for (int n = 2; n <= P; ++n) q[n] = (4.0 * (n - 1) * chi * q[n - 1] - (2.0 * n - 3.0) * q[n - 2]) / (2.0 * n - 1.0);
+    // (2n-1) q_n = 4 (n-1) chi q_{n-1} - (2n-3) q_{n-2}; counters carried in FP64, 1/(2n-1) from a table
+    double fn1 = 1.0, f2n3 = 1.0;
+    for (int n = 2; n <= P; ++n) {
+      q[n] = (4.0 * fn1 * chi * q[n - 1] - f2n3 * q[n - 2]) * inv_odd[n];
+      fn1 += 1.0;
+      f2n3 += 2.0;
+    }
   } else {
     const int n_start = P + 20 + (int)ceil(40.0 / eta);
     double rho = 0.0;
+    double fn1 = n_start - 1, f2n1 = 2 * n_start - 1;  // n - 1 and 2n - 1
     for (int n = n_start; n >= 2; --n) {
-      rho = (2.0 * n - 3.0) / (4.0 * (n - 1) * chi - (2.0 * n - 1.0) * rho);
+      rho = (f2n1 - 2.0) / (4.0 * fn1 * chi - f2n1 * rho);
       if (n - 1 <= P) q[n - 1] = rho;  // ratio q_{n-1}/q_{n-2}
+      fn1 -= 1.0;
+      f2n1 -= 2.0;
     }
     for (int n = 1; n <= P; ++n) q[n] = q[n - 1] * q[n];
   }
-  const double chi2m1 = delta * (2.0 + delta);
+  const double half_inv = 0.5 / (delta * (2.0 + delta));  // 1 / (2 (chi^2 - 1))
   for (int m = 0; m <= P; ++m) {
     const double prev = m == 0 ? q[1] : q[m - 1];
-    dq[m] = (2.0 * m - 1.0) / (2.0 * chi2m1) * (chi * q[m] - prev);
+    dq[m] = (2.0 * m - 1.0) * half_inv * (chi * q[m] - prev);
   }
 }
 
@@ -356,12 +374,15 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   const double* ad_w = ad_x + 16;
   const double* g12_x = ad_w + 16;                  // [12], inner dyadic levels
   const double* g12_w = g12_x + 12;
+  const double* bw = g12_w + 12;                    // [order] barycentric weights of the GL nodes
   const double* brk = rules + B.brk;                // panel breakpoints [n_panels + 1]
   const double s_t = 0.5 * (brk[p] + brk[p + 1]) + 0.5 * (brk[p + 1] - brk[p]) * gl_x[lt];
   const double th_t = 2.0 * M_PI * jt / nth;
+  const double inv_nth = 1.0 / nth;
   const bool kz = (k == 0.0);
   const int n1 = kz ? 0 : B.n1;
   const int M = B.M, M2 = M / 2;
+  const double twopi_M = 2.0 * M_PI / M;
   const int P = N + n1 + 2;
   double2* row = blocks + B.blk + (long long)t * nbn;
 
@@ -430,12 +451,14 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   }
   for (int j = tid; j < M; j += NT) S.ctab[j] = cospi(2.0 * j / M);
   for (int j = tid; j < nth; j += NT) sincospi(2.0 * j / nth, &S.sth[j], &S.cth[j]);
+  for (int n = tid; n <= MAXP; n += NT) S.inv_odd[n] = 1.0 / (2.0 * n - 1.0);
   __syncthreads();
   const int nq = S.nq;
 
   for (int b0 = 0; b0 < nq; b0 += BATCH) {
     const int nbatch = min(BATCH, nq - b0);
-    if (tid < nbatch) ring_node(B, rules, s_t, th_t, S.qh[b0 + tid], P, N, S.bq[tid], S.bdq[tid], S.bs[tid]);
+    if (tid < nbatch)
+      ring_node(B, rules, s_t, th_t, S.qh[b0 + tid], P, N, S.inv_odd, S.bq[tid], S.bdq[tid], S.bs[tid]);
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
       const double* sc = S.bs[bi];
@@ -448,24 +471,28 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       const int ip = S.qp[b0 + bi];
       if (tid < order) {
         const double xs = (s - brk[ip]) / (brk[ip + 1] - brk[ip]) * 2.0 - 1.0;  // panel coordinate
-        double v = 1.0;
+        // P_l(x) = w_l prod_{m != l} (x - x_m), w_l = 1 / prod_{m != l} (x_l - x_m)
+        double v = bw[tid];
         for (int mm = 0; mm < order; ++mm)
-          if (mm != tid) v *= (xs - gl_x[mm]) / (gl_x[tid] - gl_x[mm]);
+          if (mm != tid) v *= xs - gl_x[mm];
         S.pl[tid] = v;
       }
       if (farn) {
         // far ring: integrands sampled at the azimuthal nodes, times the
         // trapezoidal weight pi/N (held in dre/dim_ = double layer, tre/tim = single layer)
         const double na0 = sc[9], na1 = sc[10], nb0 = sc[11], nb1 = sc[12], nb2 = sc[13];
+        const double cal = sc[15], sal = sc[16];
+        const double wt = 2.0 * M_PI * inv_nth;
         for (int j = tid; j < nth; j += NT) {
-          const double ph = 2.0 * M_PI * j / nth - alpha;
-          const double sh2 = sin(0.5 * ph);
-          const double s2 = sh2 * sh2;
-          const double rho = sqrt(dr * dr + c * c + 4.0 * r * rt * s2);
+          // sin^2(phi/2) = (1 - cos(theta_j - alpha))/2: on a far ring (dr^2 + c^2 >= 2.7 r r~)
+          // the rounding of the difference is far below rho^2
+          const double s2 = 0.5 * (1.0 - (S.cth[j] * cal + S.sth[j] * sal));
+          const double rho2 = dr * dr + c * c + 4.0 * r * rt * s2;
+          const double inv = rsqrt(rho2), rho = rho2 * inv;
           const double radial = dr + 2.0 * rt * s2;  // r - r~ cos(phi)
           double sn, cs;
           sincos(k * rho, &sn, &cs);
-          const double inv = 1.0 / rho, f = 0.079577471545947667884 * inv;
+          const double f = 0.079577471545947667884 * inv;
           const double gr = cs * f, gi = sn * f;                               // G
           const double dpr = (-cs - k * rho * sn) * f * inv * inv, dpi = (k * rho * cs - sn) * f * inv * inv;  // G'/rho
           const double nr = na0 + na1 * S.cth[j];                              // |J| n_r
@@ -473,7 +500,6 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
           // |J| n_r K^r + |J| n_3 K^z with K^r = (G'/rho)(r - r~ cos phi), K^z = -(G'/rho) c
           const double dre_ = nr * dpr * radial - nz * dpr * c;
           const double dim = nr * dpi * radial - nz * dpi * c;
-          const double wt = 2.0 * M_PI / nth;
           S.dre[j] = wt * dre_;
           S.dim_[j] = wt * dim;
           S.tre[j] = wt * eta * gi;
@@ -496,19 +522,17 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         __syncthreads();
       } else {
       // B: scaled static modal sequences, samples of the smooth factors, cos/sin(m alpha)
+      const double inv2r = 0.5 / r;
       for (int m = tid; m <= P; m += NT) {
         const double g0 = q[m] * scale;
         S.sg0[m] = g0;
-        S.sgr[m] = dq[m] * dchi_r * scale - g0 / (2.0 * r);
+        S.sgr[m] = dq[m] * dchi_r * scale - g0 * inv2r;
         S.sgz[m] = dq[m] * dchi_z * scale;
       }
       if (!kz) {
         for (int e = tid; e <= M2; e += NT) {
           const double rho = sqrt(dr * dr + c * c + 4.0 * r * rt * S.s2tab[e]);
-          const double x = k * rho;
-          S.fs[0][e] = cos(x);
-          S.fs[1][e] = sinc_d(x);
-          S.fs[2][e] = q3_d(x);
+          smooth_factors(k * rho, &S.fs[0][e], &S.fs[1][e], &S.fs[2][e]);
         }
       }
       for (int m = tid; m <= N + 1; m += NT) sincos(m * alpha, &S.sma[m], &S.cma[m]);
@@ -525,17 +549,17 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
             if (idx >= M) idx -= M;
             sum += f[qq] * S.ctab[idx];
           }
-          S.fc[fn][n] = (2.0 * M_PI / M) * (f[0] + ((n & 1) ? -f[M2] : f[M2]) + 2.0 * sum);
+          S.fc[fn][n] = twopi_M * (f[0] + ((n & 1) ? -f[M2] : f[M2]) + 2.0 * sum);
         }
         __syncthreads();
         // C2: derived spectra (multiplying by cos(phi) averages neighbours)
-        const double k2 = k * k, k3 = k2 * k / (4.0 * M_PI);
+        const double k2 = k * k, k3 = k2 * k * INV_4PI, k1 = k * INV_4PI;
         for (int n = tid; n <= n1; n += NT) {
           const double Sm = S.fc[1][n == 0 ? 1 : n - 1], Sp = S.fc[1][n + 1];
           const double Qm = S.fc[2][n == 0 ? 1 : n - 1], Qp = S.fc[2][n + 1];
           S.hr[n] = -k2 * ((dr + rt) * S.fc[1][n] - 0.5 * rt * (Sm + Sp));
           S.hz[n] = k2 * c * S.fc[1][n];
-          S.f2[n] = k / (4.0 * M_PI) * S.fc[1][n];
+          S.f2[n] = k1 * S.fc[1][n];
           S.pr[n] = k3 * ((dr + rt) * S.fc[2][n] - 0.5 * rt * (Qm + Qp));
           S.pz[n] = -k3 * c * S.fc[2][n];
         }
@@ -562,7 +586,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
               sum += S.fc[0][an] * S.sgz[am] + S.hz[an] * S.sg0[am];
             }
           }
-          re = sum / (2.0 * M_PI);
+          re = sum * INV_2PI;
           im = m <= n1 ? (comp == 0 ? S.f2[m] : (comp == 1 ? S.pr[m] : S.pz[m])) : 0.0;
         }
         S.gre[comp][m] = re;
@@ -647,7 +671,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
             idx += j;
             if (idx >= nth) idx -= nth;
           }
-          double2 v = make_double2(sr / nth, si / nth);
+          double2 v = make_double2(sr * inv_nth, si * inv_nth);
           if (base + e == t) v.x += 0.5;
           row[base + e] = v;
         }
@@ -737,6 +761,13 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
       for (auto& v : w) v *= 0.5;
       rules.insert(rules.end(), x.begin(), x.end());
       rules.insert(rules.end(), w.begin(), w.end());
+      qams_gauss_legendre(d.order, x, w);
+      for (int l = 0; l < d.order; ++l) {
+        double prod = 1.0;
+        for (int m = 0; m < d.order; ++m)
+          if (m != l) prod *= x[l] - x[m];
+        rules.push_back(1.0 / prod);
+      }
     }
     AsmBody& A = ab[b];
     A.kind = d.profile_kind;

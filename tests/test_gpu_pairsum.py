@@ -136,3 +136,30 @@ def test_scattered_field_against_oracle():
     ctx.field(torch.from_numpy(mu).cuda(), pts, u)
     ref = np.stack([op.field(nodes, mu[:, r], pts, sc.k, sc.eta) for r in range(R)], axis=1)
     assert rel_err(u.cpu().numpy(), ref) < 1e-12
+
+
+def test_pairsum_fp64_large_phases():
+    """FP64 pair sum with k rho up to ~3300: the table-driven e^{ik rho} (k rho
+    below 3000) and the library fallback beyond it, entry by entry against
+    the oracle's explicit sums."""
+    import paper_2606_31380_b300 as q
+    rng = np.random.default_rng(8)
+    bodies = []
+    for c in [(0.0, 0.0, 0.0), (120.0, 10.0, 5.0), (210.0, -30.0, 40.0), (3.0, 1.0, -2.0)]:
+        b = scenes.random_bodies(rng, 1, 1.0, 0.5, 1, 6, 8)[0]
+        b.center = c
+        bodies.append(b)
+    sc = scenes.Scene("far apart", bodies, 15.0, 1.0, scenes.paper_direction())
+    ctx = make_ctx(sc)
+    nodes = [body_nodes(b) for b in sc.bodies]
+    sigma = scenes.rhs_seeded(ctx.N, 2, 13)
+    ref = op.pair_sum(nodes, sigma, sc.k, sc.eta)
+    got = _gpu_pairsum(ctx, sigma, q.PREC_FP64)
+    # each body's rows separately: their scales differ by the distances.  Both
+    # sides round rho differently by ~1 ulp, i.e. k rho by ~2e-13 at these
+    # distances, which sets the tolerance; a wrong table entry, index or
+    # reduction constant gives O(1) errors.
+    off = np.cumsum([0] + [b.n_nodes for b in bodies])
+    for a in range(len(bodies)):
+        rows = slice(off[a], off[a + 1])
+        assert rel_err(got[rows], ref[rows]) < FP64_TOL

@@ -39,7 +39,6 @@ namespace {
 
 constexpr int NT = 128;      // threads per CTA
 constexpr int BATCH = 16;    // outer nodes whose recursions run together (warp 0)
-constexpr int MAXQ = 1152;   // outer nodes per row
 constexpr int MAXP = 96;     // highest static mode N + n1 + 1
 constexpr int MAXM2 = 96;    // M/2 + 1 samples of the smooth factors
 constexpr int MAXN1 = 88;    // highest smooth-factor mode + 2
@@ -47,16 +46,19 @@ constexpr int MAXN = 32;     // N = n_theta / 2
 constexpr int MAXORD = 19;
 constexpr int MAXE = (MAXORD * 2 * MAXN + NT - 1) / NT;  // panel entries per thread
 
+// The outer nodes of a row come in at most four pieces (the self panel split
+// at s_t, one piece per neighbour), each K dyadic levels toward its singular
+// end plus a graded innermost panel; nodes are generated from these
+// descriptors when a batch needs them.
 struct alignas(16) RowShared {
-  // outer nodes of the row
-  double qh[MAXQ];
-  double qw[MAXQ];
-  int qp[MAXQ];
-  int nq;
-  // per-batch node data (filled by warp 0)
-  double bq[BATCH][MAXP + 1];   // Q_{m-1/2}
-  double bdq[BATCH][MAXP + 1];  // dQ_{m-1/2}/dchi
+  double pc_h0[4], pc_L[4];     // piece start (offset from s_t) and signed length
+  int pc_K[4], pc_panel[4], pc_self[4], pc_end[4];  // levels, panel, self flag, cumulative node count
+  int npc, nq;
+  // per-batch node data (filled by warp 0; Q and dQ/dchi live in dynamic shared memory)
   double bs[BATCH][18];         // scalars
+  double bw[BATCH];             // outer weights
+  int bp[BATCH];                // panels
+  int bflush[BATCH];            // 1 on the last outer node of a panel
   // per-node work arrays
   double sg0[MAXP + 1], sgr[MAXP + 1], sgz[MAXP + 1];  // static g^, d_r g^, d_z g^ (modes 0..P)
   double fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho)
@@ -334,18 +336,62 @@ __device__ void smooth_kernel(const qd4& x, const qd4& y, const qd4& n, double k
   *kim = (sn * are + cs * aim) * f;
 }
 
-__global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict__ bodies, int nb,
+// Rule tables of one order (see qams_assemble_launch for the layout).
+struct Rules {
+  const double *d0_x, *d0_w, *dy_x, *dy_w, *g12_x, *g12_w, *in_x, *in_w, *ad_x, *ad_w;
+};
+
+// Outer node `idx` of the row: offset h = s - s_t, weight, panel and whether it
+// ends its panel.  Same arithmetic, node for node, as writing the pieces out.
+__device__ void outer_node(const RowShared& S, const Rules& R, int order, int idx, double* h, double* w, int* panel,
+                           int* flush) {
+  int pc = 0;
+  while (pc + 1 < S.npc && idx >= S.pc_end[pc]) ++pc;
+  *panel = S.pc_panel[pc];
+  *flush = (idx == S.pc_end[pc] - 1) && (pc + 1 == S.npc || S.pc_panel[pc + 1] != S.pc_panel[pc]);
+  int j = idx - (pc > 0 ? S.pc_end[pc - 1] : 0);
+  const double h0 = S.pc_h0[pc], L = S.pc_L[pc], aL = fabs(L);
+  const int K = S.pc_K[pc];
+  const int ng = order + 4;
+  double top = 1.0;
+  for (int kk = 0; kk < K; ++kk) {
+    const int nk = kk == 0 ? ng + order : (kk == 1 ? ng : 12);
+    const double bot = 0.5 * top;
+    if (j < nk) {
+      const double* kx = kk == 0 ? R.d0_x : (kk == 1 ? R.dy_x : R.g12_x);
+      const double* kw = kk == 0 ? R.d0_w : (kk == 1 ? R.dy_w : R.g12_w);
+      const double v = bot + (top - bot) * kx[j];
+      *h = h0 + L * v;
+      *w = (top - bot) * kw[j] * aL;
+      return;
+    }
+    j -= nk;
+    top = bot;
+  }
+  const bool self = S.pc_self[pc] != 0;
+  const double uu = (self ? R.in_x : R.ad_x)[j];
+  const double iw = (self ? R.in_w : R.ad_w)[j];
+  const int pp = self ? 6 : 2;
+  const double up = pp == 6 ? uu * uu * uu * uu * uu * uu : uu * uu;
+  *h = h0 + L * top * up;
+  *w = top * iw * pp * (up / uu) * aL;
+}
+
+__global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restrict__ bodies, int nb,
                                                        const double* __restrict__ rules,
                                                        const qd4* __restrict__ x64, const qd4* __restrict__ n64,
                                                        const double* __restrict__ jac, double k, double eta,
                                                        long long row0, double2* __restrict__ blocks,
-                                                       unsigned long long* __restrict__ counts) {
+                                                       unsigned long long* __restrict__ counts, int pstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowShared& S = *reinterpret_cast<RowShared*>(smem_raw);
-  // modal-domain accumulators of the current panel, [order][2N] complex each for the
-  // double layer and the single layer (RowShared is 16-byte aligned, so its size is a
-  // multiple of 16 and these double2 arrays stay aligned)
-  double2* accD = reinterpret_cast<double2*>(smem_raw + sizeof(RowShared));
+  // Q_{m-1/2} and dQ/dchi of the batch, [BATCH][pstride] each (pstride >= P + 1, even),
+  // then the modal-domain accumulators of the current panel, [order][2N] complex each
+  // for the double layer and the single layer (RowShared's size is a multiple of 16,
+  // so every array stays 16-byte aligned)
+  double* bq = reinterpret_cast<double*>(smem_raw + sizeof(RowShared));
+  double* bdq = bq + BATCH * pstride;
+  double2* accD = reinterpret_cast<double2*>(bdq + BATCH * pstride);
 
   const long long g = row0 + blockIdx.x;  // global target node
   int lo = 0, hi = nb - 1;
@@ -374,6 +420,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   const double* ad_w = ad_x + 16;
   const double* g12_x = ad_w + 16;                  // [12], inner dyadic levels
   const double* g12_w = g12_x + 12;
+  const Rules RL{d0_x, d0_w, dy_x, dy_w, g12_x, g12_w, in_x, in_w, ad_x, ad_w};
   const double* bw = g12_w + 12;                    // [order] barycentric weights of the GL nodes
   const double* brk = rules + B.brk;                // panel breakpoints [n_panels + 1]
   const double s_t = 0.5 * (brk[p] + brk[p + 1]) + 0.5 * (brk[p + 1] - brk[p]) * gl_x[lt];
@@ -392,11 +439,10 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
   double far_re[MAXE], far_im[MAXE];
 #pragma unroll
   for (int qq = 0; qq < MAXE; ++qq) far_re[qq] = far_im[qq] = 0.0;
-  // outer nodes (thread 0 builds the list; panels in increasing order, contiguous)
+  // outer-node pieces (thread 0; panels in increasing order, the self panel's two pieces adjacent)
   if (tid == 0) {
-    int nq = 0;
+    int nq = 0, npc = 0;
     const double dpole = fmin(s_t + M_PI / 2, M_PI / 2 - s_t);
-    const int ng = order + 4;
     for (int i = max(0, p - 1); i <= min(B.n_panels - 1, p + 1); ++i) {
       const double plo = brk[i], phi_ = brk[i + 1];
       double s0[2], e0[2];
@@ -415,33 +461,17 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
         if (i == p) K = max(5, (int)ceil(log2(aL / (0.5 * dpole))));
         else K = max(6, (int)ceil(log2(aL / (3.2 * fabs(h0)))));
         K = min(K, 14);
-        double top = 1.0;
-        for (int kk = 0; kk < K; ++kk) {
-          const double bot = 0.5 * top;
-          const int nk = kk == 0 ? ng + order : (kk == 1 ? ng : 12);
-          const double* kx = kk == 0 ? d0_x : (kk == 1 ? dy_x : g12_x);
-          const double* kw = kk == 0 ? d0_w : (kk == 1 ? dy_w : g12_w);
-          for (int gq = 0; gq < nk && nq < MAXQ; ++gq, ++nq) {
-            const double v = bot + (top - bot) * kx[gq];
-            S.qh[nq] = h0 + L * v;
-            S.qw[nq] = (top - bot) * kw[gq] * aL;
-            S.qp[nq] = i;
-          }
-          top = bot;
-        }
-        const double* ix = (i == p) ? in_x : ad_x;
-        const double* iw = (i == p) ? in_w : ad_w;
-        const int ni = (i == p) ? 20 : 16;
-        const int pp = (i == p) ? 6 : 2;
-        for (int gq = 0; gq < ni && nq < MAXQ; ++gq, ++nq) {
-          const double uu = ix[gq];
-          const double up = pp == 6 ? uu * uu * uu * uu * uu * uu : uu * uu;
-          S.qh[nq] = h0 + L * top * up;
-          S.qw[nq] = top * iw[gq] * pp * (up / uu) * aL;
-          S.qp[nq] = i;
-        }
+        nq += (2 * order + 4) + (order + 4) + 12 * (K - 2) + (i == p ? 20 : 16);
+        S.pc_h0[npc] = h0;
+        S.pc_L[npc] = L;
+        S.pc_K[npc] = K;
+        S.pc_panel[npc] = i;
+        S.pc_self[npc] = i == p;
+        S.pc_end[npc] = nq;
+        ++npc;
       }
     }
+    S.npc = npc;
     S.nq = nq;
   }
   // row tables
@@ -457,18 +487,25 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
 
   for (int b0 = 0; b0 < nq; b0 += BATCH) {
     const int nbatch = min(BATCH, nq - b0);
-    if (tid < nbatch)
-      ring_node(B, rules, s_t, th_t, S.qh[b0 + tid], P, N, S.inv_odd, S.bq[tid], S.bdq[tid], S.bs[tid]);
+    if (tid < nbatch) {
+      double hq, wq;
+      int pq, fq;
+      outer_node(S, RL, order, b0 + tid, &hq, &wq, &pq, &fq);
+      S.bw[tid] = wq;
+      S.bp[tid] = pq;
+      S.bflush[tid] = fq;
+      ring_node(B, rules, s_t, th_t, hq, P, N, S.inv_odd, bq + tid * pstride, bdq + tid * pstride, S.bs[tid]);
+    }
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
       const double* sc = S.bs[bi];
       const double r = sc[0], rt = sc[1], c = sc[2], dr = sc[3], alpha = sc[4], scale = sc[5];
       const double dchi_r = sc[6], dchi_z = sc[7], s = sc[8];
-      const double* q = S.bq[bi];
-      const double* dq = S.bdq[bi];
+      const double* q = bq + bi * pstride;
+      const double* dq = bdq + bi * pstride;
       const bool farn = sc[14] != 0.0;
       if (tid == 0) n_far += farn ? 1 : 0;
-      const int ip = S.qp[b0 + bi];
+      const int ip = S.bp[bi];
       if (tid < order) {
         const double xs = (s - brk[ip]) / (brk[ip + 1] - brk[ip]) * 2.0 - 1.0;  // panel coordinate
         // P_l(x) = w_l prod_{m != l} (x - x_m), w_l = 1 / prod_{m != l} (x_l - x_m)
@@ -506,7 +543,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
           S.tim[j] = -wt * eta * gr;
         }
         __syncthreads();
-        const double wq = S.qw[b0 + bi];
+        const double wq = S.bw[bi];
         const int base = ip * per_panel;
 #pragma unroll
         for (int qq = 0; qq < MAXE; ++qq) {
@@ -640,7 +677,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       }
       __syncthreads();
       // F: accumulate w P_l(s) x (theta-coefficients) for the node's panel
-      const double wq = S.qw[b0 + bi];
+      const double wq = S.bw[bi];
       for (int e = tid; e < per_panel; e += NT) {
         const int l = e / nth, mm = e % nth;
         const double f = wq * S.pl[l];
@@ -653,8 +690,7 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
       }  // modal path
       // panel finished: inverse DFT of the accumulated coefficients into the row,
       //   A[t,(ip,l,j)] = (1/2N) sum_m [D_lm + |J_lj| S_lm] e^{i m theta_j}
-      const int gidx = b0 + bi;
-      if (gidx == nq - 1 || S.qp[gidx + 1] != ip) {
+      if (S.bflush[bi]) {
         const int base = ip * per_panel;
         for (int e = tid; e < per_panel; e += NT) {
           const int l = e / nth, j = e % nth;
@@ -713,7 +749,10 @@ __global__ void __launch_bounds__(NT) selfblock_kernel(const AsmBody* __restrict
 
 static_assert(sizeof(RowShared) % 16 == 0, "double2 accumulators follow RowShared");
 
-size_t qams_selfblock_smem(int max_per_panel) { return sizeof(RowShared) + 2 * sizeof(double2) * (size_t)max_per_panel; }
+// Dynamic shared memory of one CTA: RowShared, Q and dQ of a batch, two panel accumulators.
+size_t qams_selfblock_smem(int max_per_panel, int pstride) {
+  return sizeof(RowShared) + 2 * sizeof(double) * BATCH * (size_t)pstride + 2 * sizeof(double2) * (size_t)max_per_panel;
+}
 
 int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   const int nb = (int)c->bodies.size();
@@ -722,14 +761,11 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   std::vector<int> rule_off(64, -1);
   std::vector<AsmBody> ab(nb);
   long long blk = 0;
-  int max_nb = 0;
+  int max_nb = 0, pstride = 0;
   for (int b = 0; b < nb; ++b) {
     const BodyHost& bh = c->bodies[b];
     const qams_body_desc& d = bh.d;
-    // outer nodes per row, at most: four pieces (two on the self panel, one per neighbour)
-    // of (2o+4) + (o+4) + 12 x 12 + 20 nodes (14 dyadic levels and the graded innermost rule)
-    const int maxq = 4 * ((2 * d.order + 4) + (d.order + 4) + 12 * 12 + 20);
-    if (d.order > MAXORD || d.n_theta / 2 > MAXN || maxq > MAXQ) return QAMS_EINVAL;
+    if (d.order > MAXORD || d.n_theta / 2 > MAXN) return QAMS_EINVAL;
     if (rule_off[d.order] < 0) {
       rule_off[d.order] = (int)rules.size();
       std::vector<double> x, w;
@@ -797,6 +833,7 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
       return QAMS_EINVAL;
     A.rule = rule_off[d.order];
     max_nb = std::max(max_nb, d.order * d.n_theta);
+    pstride = std::max(pstride, (d.n_theta / 2 + A.n1 + 2 + 1 + 1) & ~1);  // P + 1, rounded up to even
   }
   int rc;
   qams_dev_free(c, &c->blocks64);
@@ -809,15 +846,17 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   QAMS_CUDA(cudaMemcpy(d_rules.p, rules.data(), sizeof(double) * rules.size(), cudaMemcpyHostToDevice));
   if ((rc = qams_dev_alloc(c, &d_counts, 2 * sizeof(unsigned long long)))) return rc;
   QAMS_CUDA(cudaMemsetAsync(d_counts.p, 0, 2 * sizeof(unsigned long long), st));
-  const size_t smem = qams_selfblock_smem(max_nb);
+  const size_t smem = qams_selfblock_smem(max_nb, pstride);
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   const long long chunk = 1 << 20;
   for (long long r0 = 0; r0 < c->N; r0 += chunk) {
     const long long n = std::min(chunk, c->N - r0);
     selfblock_kernel<<<(unsigned)n, NT, smem, st>>>((const AsmBody*)d_bodies.p, nb, (const double*)d_rules.p,
                                                     (const qd4*)c->x64.p, (const qd4*)c->n64.p,
                                                     (const double*)c->jac64.p, c->k, c->eta, r0,
-                                                    (double2*)c->blocks64.p, (unsigned long long*)d_counts.p); qams_count_launch();
+                                                    (double2*)c->blocks64.p, (unsigned long long*)d_counts.p,
+                                                    pstride); qams_count_launch();
     QAMS_CUDA(cudaGetLastError());
   }
   QAMS_CUDA(cudaStreamSynchronize(st));

@@ -124,6 +124,60 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
+# FP32 pair (R = 1): 34 FP32 operations + 4 MUFU (rsqrt, rcp, sin, cos) + 4 FMA per
+# right-hand side; FP64 pair: 44 FP64 operations + rsqrt (counted as 4) incl. the
+# table-driven e^{ik rho} (15) -- counted from the kernel sources.
+FP32_OPS_PER_PAIR = 34
+FP64_OPS_PER_PAIR = 48
+
+
+def _time_ms(torch, fn, reps=5):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def kernel_rooflines(torch, q, ctx, sc, N, R, pairs, device):
+    """Pair sums (ALU: FP32 pipe + MUFU, FP64 pipe) and block products (HBM),
+    each timed alone with CUDA events on the current stream."""
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    f = 2.032e9  # maximum SM clock (the sampled clock sits there under this load)
+    hbm = measured_peaks()[0]["hbm_gbs"]
+    s32 = torch.randn((N, R), dtype=torch.complex64, device="cuda")
+    y32 = torch.empty_like(s32)
+    s64 = s32.to(torch.complex128)
+    y64 = torch.empty_like(s64)
+    t32 = _time_ms(torch, lambda: ctx.pairsum(s32, y32, q.PREC_FP32))
+    t64 = _time_ms(torch, lambda: ctx.pairsum(s64, y64, q.PREC_FP64), reps=2)
+    # FP32: min over the FP32 pipe (128 lanes/SM/clk) and MUFU (16/SM/clk, 4 per pair)
+    peak32 = min(128 * sms * f / (FP32_OPS_PER_PAIR + 4 * R), 16 * sms * f / 4)
+    peak64 = 2 * sms * f / (FP64_OPS_PER_PAIR + 4 * (R - 1))  # FP64 pipe: 2 lanes/SM/clk
+    entries = sum(b.n_nodes ** 2 for b in sc.bodies)
+    tb32 = _time_ms(torch, lambda: ctx.selfblock_apply(s32, y32, q.PREC_FP32))
+    tb64 = _time_ms(torch, lambda: ctx.selfblock_apply(s64, y64, q.PREC_FP64))
+    reps16 = (R + 15) // 16
+    gb32 = entries * 8 * reps16 / (tb32 / 1e3) / 1e9
+    gb64 = entries * 16 * reps16 / (tb64 / 1e3) / 1e9
+    return {
+        "pairsum_f32_kernel": {"ms": t32, "pairs_per_s": pairs / (t32 / 1e3), "bound": "alu",
+                               "peak_pairs_per_s": peak32, "frac": pairs / (t32 / 1e3) / peak32},
+        "pairsum_f64_kernel": {"ms": t64, "pairs_per_s": pairs / (t64 / 1e3), "bound": "alu (FP64 pipe)",
+                               "peak_pairs_per_s": peak64, "frac": pairs / (t64 / 1e3) / peak64},
+        "block_apply_kernel<float2>": {"ms": tb32, "achieved": gb32, "peak": hbm, "unit": "GB/s",
+                                       "bound": "hbm", "frac": gb32 / hbm},
+        "block_apply_kernel<double2>": {"ms": tb64, "achieved": gb64, "peak": hbm, "unit": "GB/s",
+                                        "bound": "hbm", "frac": gb64 / hbm},
+        "note": "pair peaks from the op counts above at the maximum SM clock; HBM peak of measured",
+    }
+
+
 def assembly_flops(scene, counts):
     """Algorithmic FP64 operations of one self-block assembly, counted from the
     kernel's dense loops: per modal outer node the cosine transforms,
@@ -271,6 +325,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     apply_ms = e0.elapsed_time(e1) / 5
 
+    # the other hot kernels alone, each against its own roofline
+    kernels = kernel_rooflines(torch, q, ctx, sc, N, R, pairs, local_rank)
+
     # e2e: through the C ABI from host descriptors to host results
     e2e_steps = max(1, min(args.steps, 3))
     mu_h = torch.empty((N, R), dtype=torch.complex128, pin_memory=True)
@@ -335,6 +392,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
+        "kernels": kernels,
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)

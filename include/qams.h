@@ -186,6 +186,17 @@ int qams_copy_preconditioner(const qams_ctx* ctx, int body, void* dst_dev, void*
  * qams_assemble.  Uses a library-owned workspace of N*R complex. */
 int qams_apply(qams_ctx* ctx, int R, const void* x_dev, void* y_dev, int precision, void* stream);
 
+/* Block-diagonal products (the self-block and preconditioner rows of the
+ * operator, Eq. linearsys): y_b = A_b x_b (qams_selfblock_apply) or
+ * y_b = P_b x_b with P_b = A_b^{-1} (qams_precond_apply) for every body, no
+ * inter-body part.  x, y: [N][R], complex128 (FP64, the complex128 blocks; the
+ * preconditioner's complex64 inverse widened) or complex64 (FP32, the
+ * complex64 copies).  QAMS_EINVAL before qams_assemble / before the
+ * preconditioner exists.  HBM-bound: every call streams all blocks once per
+ * 16 right-hand sides. */
+int qams_selfblock_apply(qams_ctx* ctx, int R, const void* x_dev, void* y_dev, int precision, void* stream);
+int qams_precond_apply(qams_ctx* ctx, int R, const void* x_dev, void* y_dev, int precision, void* stream);
+
 /* Solver options (Sec. 6: GMRES; restart, tolerances and orthogonalisation
  * are not stated by the paper).  precision = QAMS_PREC_FP64: restarted
  * GMRES with the FP64 apply, stop at ||b - A mu|| <= tol ||b|| per column.

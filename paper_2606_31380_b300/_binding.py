@@ -92,6 +92,8 @@ def load_library():
         "qams_solve": (i, [vp, i, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveStats), vp]),
         "qams_farfield": (i, [vp, i, vp, i, vp, vp, vp]),
         "qams_field": (i, [vp, i, vp, i, vp, vp, vp]),
+        "qams_selfblock_apply": (i, [vp, i, vp, vp, i, vp]),
+        "qams_precond_apply": (i, [vp, i, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -266,6 +268,21 @@ class Context:
         dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
         _check(self.lib.qams_apply(self._h, R, _dev(x, dt, (self.N, R), "x"), _dev(y, dt, (self.N, R), "y"),
                                    precision, C.c_void_p(_stream_ptr(stream))), "qams_apply")
+
+    def selfblock_apply(self, x, y, precision: int = PREC_FP64, stream=None):
+        """y_b = A_b x_b for every body (no inter-body part)."""
+        self._diag("qams_selfblock_apply", x, y, precision, stream)
+
+    def precond_apply(self, x, y, precision: int = PREC_FP64, stream=None):
+        """y_b = P_b x_b, P_b = A_b^{-1} (after build_preconditioner or a preconditioned solve)."""
+        self._diag("qams_precond_apply", x, y, precision, stream)
+
+    def _diag(self, name, x, y, precision, stream):
+        import torch
+        dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
+        R = x.shape[1]
+        _check(getattr(self.lib, name)(self._h, R, _dev(x, dt, (self.N, R), "x"), _dev(y, dt, (self.N, R), "y"),
+                                       precision, C.c_void_p(_stream_ptr(stream))), name)
 
     def solve(self, rhs, mu, precision: int = PREC_FP32, tol: float = None, restart: int = None,
               max_iters: int = None, inner_tol: float = None, precondition: bool = True, stream=None,

@@ -243,6 +243,24 @@ int qams_apply(qams_ctx* c, int R, const void* x, void* y, int precision, void* 
   return qams_apply_launch(c, R, x, y, precision, (cudaStream_t)stream);
 }
 
+static int block_apply_diag(qams_ctx* c, int which, int R, const void* x, void* y, int precision, void* stream) {
+  if (!c || R < 1 || !x || !y || !c->assembled || (which != 0 && which != 1)) return QAMS_EINVAL;
+  if (precision != QAMS_PREC_FP64 && precision != QAMS_PREC_FP32) return QAMS_EINVAL;
+  if (which == 1 && !c->have_precond) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  const void* blocks = which == 0 ? (precision == QAMS_PREC_FP64 ? c->blocks64.p : c->blocks32.p)
+                                  : (precision == QAMS_PREC_FP64 ? c->pinv64.p : c->pinv32.p);
+  return qams_block_apply_ptr(c, blocks, R, x, y, precision, false, (cudaStream_t)stream);
+}
+
+int qams_selfblock_apply(qams_ctx* c, int R, const void* x, void* y, int precision, void* stream) {
+  return block_apply_diag(c, 0, R, x, y, precision, stream);
+}
+
+int qams_precond_apply(qams_ctx* c, int R, const void* x, void* y, int precision, void* stream) {
+  return block_apply_diag(c, 1, R, x, y, precision, stream);
+}
+
 int qams_incident_plane(qams_ctx* c, int R, const double* dirs, void* rhs, void* stream) {
   if (!c || R < 1 || !dirs || !rhs || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
   QAMS_CUDA(cudaSetDevice(c->device));

@@ -163,6 +163,24 @@ def test_block_jacobi_preconditioner():
         ctx.copy_preconditioner(bi, P)
         E = (P @ A).cpu().numpy() - np.eye(n)
         assert np.max(np.abs(E)) < 1e-3
+    # the block-diagonal products through the C ABI, R = 3 (FP64 and FP32)
+    x = torch.from_numpy(scenes.rhs_seeded(ctx.N, 3, 21)).cuda()
+    for prec, dt, tol in [(q.PREC_FP64, torch.complex128, 1e-14), (q.PREC_FP32, torch.complex64, 1e-5)]:
+        ya = torch.full_like(x.to(dt), float("nan"))
+        yp = torch.full_like(x.to(dt), float("nan"))
+        ctx.selfblock_apply(x.to(dt).contiguous(), ya, prec)
+        ctx.precond_apply(x.to(dt).contiguous(), yp, prec)
+        for bi in range(len(bodies)):
+            n = int(off[bi + 1] - off[bi])
+            rows = slice(int(off[bi]), int(off[bi + 1]))
+            A = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+            P = torch.zeros_like(A)
+            ctx.copy_selfblock(bi, A)
+            ctx.copy_preconditioner(bi, P)
+            refa = (A @ x[rows]).cpu().numpy()
+            refp = (P @ x[rows]).cpu().numpy()
+            assert np.max(np.abs(ya[rows].cpu().numpy() - refa)) < tol * np.max(np.abs(refa))
+            assert np.max(np.abs(yp[rows].cpu().numpy() - refp)) < tol * np.max(np.abs(refp))
     b = torch.zeros((ctx.N, 1), dtype=torch.complex128, device="cuda")
     ctx.incident_plane(sc.directions, b)
     m0 = torch.zeros_like(b)

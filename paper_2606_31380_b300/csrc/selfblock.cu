@@ -60,12 +60,14 @@ struct alignas(16) RowShared {
   int bp[BATCH];                // panels
   int bflush[BATCH];            // 1 on the last outer node of a panel
   // per-node work arrays
-  double sg0[MAXP + 1], sgr[MAXP + 1], sgz[MAXP + 1];  // static g^, d_r g^, d_z g^ (modes 0..P)
+  double sg0[MAXP + 1], sdq[MAXP + 1];  // static g^ and Q'(chi) scale (modes 0..P)
   double fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho)
   double fc[3][MAXN1 + 1];      // their cosine coefficients
-  double hr[MAXN1 + 1], hz[MAXN1 + 1], pr[MAXN1 + 1], pz[MAXN1 + 1], f2[MAXN1 + 1];
+  double pr[MAXN1 + 1], pz[MAXN1 + 1], f2[MAXN1 + 1];
+  double cA[MAXN + 2], cB[MAXN + 2], cC[MAXN + 3];  // the three phi-convolutions (see stage D)
   double gre[3][MAXN + 2], gim[3][MAXN + 2];  // G^, d_r G^, d_z G^ (phi coefficients, m <= N+1)
   double cma[MAXN + 2], sma[MAXN + 2];         // cos(m alpha), sin(m alpha)
+  double ecs[8 + (MAXN + 9) / 8], esn[8 + (MAXN + 9) / 8];  // cos/sin(j alpha), j < 8, then of 8 l alpha
   double dre[2 * MAXN], dim_[2 * MAXN];        // theta-coefficients of the double-layer integrand
   double tre[2 * MAXN], tim[2 * MAXN];         // theta-coefficients of the single-layer integrand
   double pl[MAXORD];
@@ -559,12 +561,11 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
         __syncthreads();
       } else {
       // B: scaled static modal sequences, samples of the smooth factors, cos/sin(m alpha)
-      const double inv2r = 0.5 / r;
+      // static coefficients: g^_m = Q scale, d_r g^_m = dchi_r Q' scale - g^_m/(2r),
+      // d_z g^_m = dchi_z Q' scale -- all from g^ and Q' scale
       for (int m = tid; m <= P; m += NT) {
-        const double g0 = q[m] * scale;
-        S.sg0[m] = g0;
-        S.sgr[m] = dq[m] * dchi_r * scale - g0 * inv2r;
-        S.sgz[m] = dq[m] * dchi_z * scale;
+        S.sg0[m] = q[m] * scale;
+        S.sdq[m] = dq[m] * scale;
       }
       if (!kz) {
         for (int e = tid; e <= M2; e += NT) {
@@ -572,7 +573,11 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
           smooth_factors(k * rho, &S.fs[0][e], &S.fs[1][e], &S.fs[2][e]);
         }
       }
-      for (int m = tid; m <= N + 1; m += NT) sincos(m * alpha, &S.sma[m], &S.cma[m]);
+      // e^{i m alpha} = e^{i 8 l alpha} e^{i j alpha}, m = 8 l + j: 13 sincos, combined in D2
+      if (tid < 8 + (N + 2 + 7) / 8) {
+        const int j = tid < 8 ? tid : 8 * (tid - 8);
+        sincos(j * alpha, &S.esn[tid], &S.ecs[tid]);
+      }
       __syncthreads();
       if (!kz) {
         // C1: cosine coefficients f^_n = (2pi/M)[f_0 + (-1)^n f_{M/2} + 2 sum f_q cos(2 pi n q/M)]
@@ -589,45 +594,57 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
           S.fc[fn][n] = twopi_M * (f[0] + ((n & 1) ? -f[M2] : f[M2]) + 2.0 * sum);
         }
         __syncthreads();
-        // C2: derived spectra (multiplying by cos(phi) averages neighbours)
-        const double k2 = k * k, k3 = k2 * k * INV_4PI, k1 = k * INV_4PI;
+        // C2: spectra of the smooth imaginary parts (multiplying by cos(phi) averages neighbours)
+        const double k3 = k * k * k * INV_4PI, k1 = k * INV_4PI;
         for (int n = tid; n <= n1; n += NT) {
-          const double Sm = S.fc[1][n == 0 ? 1 : n - 1], Sp = S.fc[1][n + 1];
           const double Qm = S.fc[2][n == 0 ? 1 : n - 1], Qp = S.fc[2][n + 1];
-          S.hr[n] = -k2 * ((dr + rt) * S.fc[1][n] - 0.5 * rt * (Sm + Sp));
-          S.hz[n] = k2 * c * S.fc[1][n];
           S.f2[n] = k1 * S.fc[1][n];
           S.pr[n] = k3 * ((dr + rt) * S.fc[2][n] - 0.5 * rt * (Qm + Qp));
           S.pz[n] = -k3 * c * S.fc[2][n];
         }
+        // D: the three convolutions the real parts need (all sequences even in n),
+        //   A_m = sum_n cos^_n g^_{m-n},  B_m = sum_n cos^_n (Q' scale)_{m-n},
+        //   C_m = sum_n sinc^_n g^_{m-n}   (m = 0..N+1; C also at N+2),
+        // because d_r g^ and d_z g^ are combinations of g^ and Q' scale, and the
+        // sinc-weighted terms are C_m and its cos(phi)-shift (C_{m-1} + C_{m+1})/2.
+        const int L0 = N + 2;
+        for (int e = tid; e < 3 * L0 + 1; e += NT) {
+          const double* f = e < 2 * L0 ? S.fc[0] : S.fc[1];
+          const double* g = (e >= L0 && e < 2 * L0) ? S.sdq : S.sg0;
+          const int m = e < L0 ? e : (e < 2 * L0 ? e - L0 : e - 2 * L0);
+          double sum = f[0] * g[m];
+          for (int n = 1; n <= n1; ++n) sum += f[n] * g[abs(m - n)] + f[n] * g[m + n];
+          (e < L0 ? S.cA : (e < 2 * L0 ? S.cB : S.cC))[m] = sum;
+        }
         __syncthreads();
       }
-      // D: modal coefficients of G, d_r G, d_z G for m = 0..N+1
-      for (int e = tid; e < 3 * (N + 2); e += NT) {
-        const int comp = e / (N + 2), m = e % (N + 2);
-        double re, im = 0.0;
-        if (kz) {
-          re = comp == 0 ? S.sg0[m] : (comp == 1 ? S.sgr[m] : S.sgz[m]);
-        } else {
-          double sum = 0.0;
-          if (comp == 0) {
-            for (int n = -n1; n <= n1; ++n) sum += S.fc[0][abs(n)] * S.sg0[abs(m - n)];
+      // D2: modal coefficients of G, d_r G, d_z G for m = 0..N+1, and cos/sin(m alpha)
+      for (int m = tid; m <= N + 1; m += NT) {
+        const int l = 8 + (m >> 3), j = m & 7;
+        S.cma[m] = S.ecs[l] * S.ecs[j] - S.esn[l] * S.esn[j];
+        S.sma[m] = S.esn[l] * S.ecs[j] + S.ecs[l] * S.esn[j];
+      }
+      {
+        const double inv2r = 0.5 / r, k2 = k * k;
+        for (int e = tid; e < 3 * (N + 2); e += NT) {
+          const int comp = e / (N + 2), m = e % (N + 2);
+          double re, im = 0.0;
+          if (kz) {
+            re = comp == 0 ? S.sg0[m] : (comp == 1 ? dchi_r * S.sdq[m] - S.sg0[m] * inv2r : dchi_z * S.sdq[m]);
+          } else if (comp == 0) {
+            re = S.cA[m] * INV_2PI;
+            im = m <= n1 ? S.f2[m] : 0.0;
           } else if (comp == 1) {
-            for (int n = -n1; n <= n1; ++n) {
-              const int an = abs(n), am = abs(m - n);
-              sum += S.fc[0][an] * S.sgr[am] + S.hr[an] * S.sg0[am];
-            }
+            const double cbar = 0.5 * (S.cC[m == 0 ? 1 : m - 1] + S.cC[m + 1]);
+            re = (dchi_r * S.cB[m] - S.cA[m] * inv2r - k2 * ((dr + rt) * S.cC[m] - rt * cbar)) * INV_2PI;
+            im = m <= n1 ? S.pr[m] : 0.0;
           } else {
-            for (int n = -n1; n <= n1; ++n) {
-              const int an = abs(n), am = abs(m - n);
-              sum += S.fc[0][an] * S.sgz[am] + S.hz[an] * S.sg0[am];
-            }
+            re = (dchi_z * S.cB[m] + k2 * c * S.cC[m]) * INV_2PI;
+            im = m <= n1 ? S.pz[m] : 0.0;
           }
-          re = sum * INV_2PI;
-          im = m <= n1 ? (comp == 0 ? S.f2[m] : (comp == 1 ? S.pr[m] : S.pz[m])) : 0.0;
+          S.gre[comp][m] = re;
+          S.gim[comp][m] = im;
         }
-        S.gre[comp][m] = re;
-        S.gim[comp][m] = im;
       }
       __syncthreads();
       // E: theta-coefficients, index m = -N+1..N stored at m mod 2N (the entry at N is the

@@ -192,14 +192,18 @@ def assembly_flops(scene, counts):
     for b in scene.bodies:
         order, nth, npan = b.order, b.n_theta, b.n_panels
         N = nth // 2
-        amp = sum(abs(x) for x in b.mode_cos) + sum(abs(x) for x in b.mode_sin)
-        n1 = math.ceil(1.3 * scene.k * b.base_radius * (1 + amp) + 16.0)
+        if getattr(b, "kind", 0) == 1:
+            rmax = sum(abs(A) + abs(B) for (_, A, B) in b.series[3])
+        else:
+            rmax = b.base_radius * (1 + sum(abs(x) for x in b.mode_cos) + sum(abs(x) for x in b.mode_sin))
+        n1 = math.ceil(1.3 * scene.k * rmax + 16.0)
         M2 = n1 + 8
         w = b.n_nodes
         wsum += w
-        # cosine DFTs of 3 smooth factors, convolutions (3 kernels, modes 0..N+1),
+        # cosine DFTs of 3 smooth factors, three convolutions (modes 0..N+1, one to N+2),
         # theta-coefficients of the two integrands, accumulation
-        per_node += w * (6 * (n1 + 2) * (M2 - 1) + 10 * (N + 2) * (2 * n1 + 1) + 40 * nth + 8 * order * nth)
+        per_node += w * (6 * (n1 + 2) * (M2 - 1) + 2 * (3 * (N + 2) + 1) * (2 * n1 + 1) + 40 * nth
+                         + 8 * order * nth)
         per_far += w * (30 * nth + 8 * order * nth)
         # every row: inverse DFT per near panel
         near = sum(min(npan - 1, p + 1) - max(0, p - 1) + 1 for p in range(npan)) * order * nth

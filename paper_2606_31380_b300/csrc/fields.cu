@@ -2,6 +2,7 @@
 // far-field pattern of the combined-layer density.
 #include <cmath>
 
+#include "phase.cuh"
 #include "qams_internal.h"
 
 namespace {
@@ -28,6 +29,9 @@ __global__ void farfield_kernel(const qd4* __restrict__ x, const qd4* __restrict
                                 const double* __restrict__ dirs, double k, double eta,
                                 double2* __restrict__ uinf) {
   __shared__ double2 red[256];
+  __shared__ double2 ph[PH_N];
+  phase_table_fill(ph);
+  __syncthreads();
   const int m = blockIdx.x;
   const double hx = dirs[3 * m], hy = dirs[3 * m + 1], hz = dirs[3 * m + 2];
   double2 acc[MAXR];
@@ -36,7 +40,7 @@ __global__ void farfield_kernel(const qd4* __restrict__ x, const qd4* __restrict
     const qd4 p = x[s];
     const qd4 q = n[s];
     double sn, cs;
-    sincos(-k * (hx * p.x + hy * p.y + hz * p.z), &sn, &cs);
+    sincos_table(-k * (hx * p.x + hy * p.y + hz * p.z), ph, &sn, &cs);
     // (-ik xhat.n - i eta) e^{-ik xhat.y} w
     const double fi = -(k * (hx * q.x + hy * q.y + hz * q.z) + eta) * p.w;
     const double fre = -sn * fi, fim = cs * fi;

@@ -16,6 +16,7 @@
 // part e^{ik rho0} is applied once per (target, source body) in FP64.
 #include <cmath>
 
+#include "phase.cuh"
 #include "qams_internal.h"
 
 namespace {
@@ -127,41 +128,6 @@ __global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
   }
 }
 
-// e^{i phi} for the FP64 path by the accurate-table method (Gal 1986; Tang,
-// ACM TOMS 1989/1990): phi = j h + t with h = 2 pi / PH_N and |t| <= h/2,
-// then sin(jh + t) = s_j cos t + c_j sin t, cos(jh + t) = c_j cos t - s_j sin t.
-// j = rint(phi / h) by adding 1.5 * 2^52 (its low mantissa bits hold j);
-// t = phi - j C1 - j C2 with C1 = h rounded to 36 bits (j C1 exact for
-// j < 2^17) and C2 = the next 53 bits of h (both from a 60-digit value of
-// pi); |t| <= 0.0123, so the Taylor polynomials of degree 5 (sin) and 6
-// (cos) are exact to 1e-17.  Arguments beyond PH_MAX (never reached by these
-// geometries: k rho < 3000) take the library sincos.
-constexpr int PH_N = 256;
-constexpr double PH_INV_H = 40.74366543152521;           // PH_N / (2 pi)
-constexpr double PH_C1 = 0x1.921fb54440000p-6;           // 2 pi / PH_N, 36 bits
-constexpr double PH_C2 = 0x1.68c234c4c6629p-45;          // 2 pi / PH_N - PH_C1
-constexpr double PH_MAX = 3000.0;                        // j < 2^17
-constexpr double PH_ROUND = 6755399441055744.0;          // 1.5 * 2^52
-
-__device__ __forceinline__ void sincos_table(double phi, const double2* __restrict__ tab, double* sn,
-                                             double* cs) {
-  if (!(phi < PH_MAX) || phi < 0.0) {
-    sincos(phi, sn, cs);
-    return;
-  }
-  const double big = fma(phi, PH_INV_H, PH_ROUND);
-  const int j = __double2loint(big) & (PH_N - 1);
-  const double jd = big - PH_ROUND;
-  double t = fma(-jd, PH_C1, phi);
-  t = fma(-jd, PH_C2, t);
-  const double t2 = t * t;
-  const double st = fma(fma(0x1.1111111111111p-7, t2, -0x1.5555555555555p-3) * t2, t, t);  // t - t^3/6 + t^5/120
-  const double ct = fma(fma(fma(-0x1.6c16c16c16c17p-10, t2, 0x1.5555555555555p-5), t2, -0.5), t2, 1.0);
-  const double2 e = tab[j];  // (cos, sin)(j h)
-  *sn = fma(e.y, ct, e.x * st);
-  *cs = fma(e.x, ct, -(e.y * st));
-}
-
 template <int RC>
 __global__ void __launch_bounds__(TILE) pairsum_f64_kernel(
     const TargetTile* __restrict__ tiles, const SourceSplit* __restrict__ splits,
@@ -173,11 +139,7 @@ __global__ void __launch_bounds__(TILE) pairsum_f64_kernel(
   __shared__ double2 ss[CHUNK][RC];
   __shared__ double2 ph[PH_N];
 
-  for (int j = threadIdx.x; j < PH_N; j += blockDim.x) {
-    double sv, cv;
-    sincospi(2.0 * j / PH_N, &sv, &cv);
-    ph[j] = make_double2(cv, sv);
-  }
+  phase_table_fill(ph);
   const TargetTile tile = tiles[blockIdx.x];
   const SourceSplit split = splits[blockIdx.y];
   const int tid = threadIdx.x;

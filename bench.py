@@ -172,8 +172,12 @@ def kernel_rooflines(torch, q, ctx, sc, N, R, pairs, device):
                                "peak_pairs_per_s": peak64, "frac": pairs / (t64 / 1e3) / peak64},
         "block_apply_kernel<float2>": {"ms": tb32, "achieved": gb32, "peak": hbm, "unit": "GB/s",
                                        "bound": "hbm", "frac": gb32 / hbm},
-        "block_apply_kernel<double2>": {"ms": tb64, "achieved": gb64, "peak": hbm, "unit": "GB/s",
-                                        "bound": "hbm", "frac": gb64 / hbm},
+        # complex128 entries: 4 FP64 operations per entry and right-hand side put the
+        # FP64 pipe (2 lanes/SM/clk) below the HBM stream
+        "block_apply_kernel<double2>": {"ms": tb64, "achieved": entries * R / (tb64 / 1e3), "unit": "entries/s",
+                                        "bound": "alu (FP64 pipe)", "peak": 2 * sms * f / 4,
+                                        "frac": entries * R / (tb64 / 1e3) / (2 * sms * f / 4),
+                                        "hbm_gbs": gb64},
         "note": "pair peaks from the op counts above at the maximum SM clock; HBM peak of measured",
     }
 

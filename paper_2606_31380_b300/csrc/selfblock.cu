@@ -305,7 +305,9 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
       f2n3 += 2.0;
     }
   } else {
-    const int n_start = P + 20 + (int)ceil(40.0 / eta);
+    // Miller's start: its error at index n <= P decays like e^{-2 (n_start - n) eta}
+    // (minimal against dominant solution), so P + 10 + 20/eta leaves e^{-40}
+    const int n_start = P + 10 + (int)ceil(20.0 / eta);
     double rho = 0.0;
     double fn1 = n_start - 1, f2n1 = 2 * n_start - 1;  // n - 1 and 2n - 1
     for (int n = n_start; n >= 2; --n) {
@@ -510,8 +512,8 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       const int ip = S.bp[bi];
       if (tid < order) {
         const double xs = (s - brk[ip]) / (brk[ip + 1] - brk[ip]) * 2.0 - 1.0;  // panel coordinate
-        // P_l(x) = w_l prod_{m != l} (x - x_m), w_l = 1 / prod_{m != l} (x_l - x_m)
-        double v = bw[tid];
+        // outer weight times P_l(x), P_l(x) = w_l prod_{m != l} (x - x_m), w_l = 1 / prod_{m != l} (x_l - x_m)
+        double v = bw[tid] * S.bw[bi];
         for (int mm = 0; mm < order; ++mm)
           if (mm != tid) v *= xs - gl_x[mm];
         S.pl[tid] = v;
@@ -545,7 +547,6 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
           S.tim[j] = -wt * eta * gr;
         }
         __syncthreads();
-        const double wq = S.bw[bi];
         const int base = ip * per_panel;
 #pragma unroll
         for (int qq = 0; qq < MAXE; ++qq) {
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
           if (e < per_panel) {
             const int l = e / nth, j = e % nth;
             const double J = jac[B.offset + base + e];
-            const double f = wq * S.pl[l];
+            const double f = S.pl[l];
             far_re[qq] += f * (S.dre[j] + J * S.tre[j]);
             far_im[qq] += f * (S.dim_[j] + J * S.tim[j]);
           }
@@ -694,10 +695,9 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       }
       __syncthreads();
       // F: accumulate w P_l(s) x (theta-coefficients) for the node's panel
-      const double wq = S.bw[bi];
       for (int e = tid; e < per_panel; e += NT) {
         const int l = e / nth, mm = e % nth;
-        const double f = wq * S.pl[l];
+        const double f = S.pl[l];
         accD[e].x += f * S.dre[mm];
         accD[e].y += f * S.dim_[mm];
         accS[e].x += f * S.tre[mm];

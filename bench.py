@@ -129,6 +129,9 @@ def fp64_peak_tflops(torch):
 # table-driven e^{ik rho} (15) -- counted from the kernel sources.
 FP32_OPS_PER_PAIR = 34
 FP64_OPS_PER_PAIR = 48
+# float-float pair: ~640 FP32 operations (the e^{ik rho} evaluation ~195, the
+# accumulation 72 per right-hand side) -- counted from the kernel source
+FF_OPS_PER_PAIR = 640
 
 
 def _time_ms(torch, fn, reps=5):
@@ -156,6 +159,10 @@ def kernel_rooflines(torch, q, ctx, sc, N, R, pairs, device):
     y64 = torch.empty_like(s64)
     t32 = _time_ms(torch, lambda: ctx.pairsum(s32, y32, q.PREC_FP32))
     t64 = _time_ms(torch, lambda: ctx.pairsum(s64, y64, q.PREC_FP64), reps=2)
+    yff = torch.empty_like(s64)
+    tff = _time_ms(torch, lambda: ctx.pairsum(s64, yff, q.PREC_FF), reps=3)
+    ff_diff = float(torch.linalg.norm(yff - y64) / torch.linalg.norm(y64))
+    peakff = 128 * sms * f / (FF_OPS_PER_PAIR + 72 * (R - 1))
     # FP32: min over the FP32 pipe (128 lanes/SM/clk) and MUFU (16/SM/clk, 4 per pair)
     peak32 = min(128 * sms * f / (FP32_OPS_PER_PAIR + 4 * R), 16 * sms * f / 4)
     peak64 = 2 * sms * f / (FP64_OPS_PER_PAIR + 4 * (R - 1))  # FP64 pipe: 2 lanes/SM/clk
@@ -170,6 +177,9 @@ def kernel_rooflines(torch, q, ctx, sc, N, R, pairs, device):
                                "peak_pairs_per_s": peak32, "frac": pairs / (t32 / 1e3) / peak32},
         "pairsum_f64_kernel": {"ms": t64, "pairs_per_s": pairs / (t64 / 1e3), "bound": "alu (FP64 pipe)",
                                "peak_pairs_per_s": peak64, "frac": pairs / (t64 / 1e3) / peak64},
+        "pairsum_ff_kernel": {"ms": tff, "pairs_per_s": pairs / (tff / 1e3), "bound": "alu (FP32 pipe)",
+                              "peak_pairs_per_s": peakff, "frac": pairs / (tff / 1e3) / peakff,
+                              "rel_diff_vs_fp64_kernel": ff_diff},
         "block_apply_kernel<float2>": {"ms": tb32, "achieved": gb32, "peak": hbm, "unit": "GB/s",
                                        "bound": "hbm", "frac": gb32 / hbm},
         # complex128 entries: 4 FP64 operations per entry and right-hand side put the

@@ -51,7 +51,11 @@ enum {
   QAMS_EAGAIN = -10     /* request not finished yet (qams_poll)           */
 };
 
-enum { QAMS_PREC_FP64 = 0, QAMS_PREC_FP32 = 1 };
+/* Arithmetic of the operator calls.  QAMS_PREC_FF: complex128 vectors and
+ * FP64 block products, with the pair sum in float-float arithmetic (pairs of
+ * FP32 numbers, ~48 bits: relative error ~1e-14 per pair) -- FP64-accurate
+ * results without B300's slow FP64 pipe.  Used by qams_pairsum and qams_apply. */
+enum { QAMS_PREC_FP64 = 0, QAMS_PREC_FP32 = 1, QAMS_PREC_FF = 2 };
 
 typedef struct qams_ctx qams_ctx; /* opaque, library-owned */
 
@@ -139,7 +143,8 @@ int qams_set_wavenumber(qams_ctx* ctx, double k, double eta);
  * y_dev are [N][R] complex of the given precision; y is overwritten.
  * QAMS_PREC_FP32 evaluates each pair in FP32 with the phase split per body
  * pair, e^{ik rho} = e^{ik rho_0} e^{ik (rho - rho_0)}, rho_0 = |c_a - c_b|
- * in FP64.  Errors: QAMS_EINVAL (R < 1, no bodies, no wavenumber). */
+ * in FP64; QAMS_PREC_FF does the same split in float-float arithmetic on
+ * complex128 data.  Errors: QAMS_EINVAL (R < 1, no bodies, no wavenumber). */
 int qams_pairsum(qams_ctx* ctx, int R, const void* sigma_dev, void* y_dev, int precision, void* stream);
 
 /* Self-block assembly (Sec. 3.1-3.4): for every body the dense n_b x n_b
@@ -218,6 +223,8 @@ typedef struct {
   double inner_tol; /* FP32 mode: reduction per correction */
   int max_refine;   /* FP32 mode: corrections */
   int precondition; /* 1: right block-Jacobi preconditioning (built on first use) */
+  int residual;     /* FP32 mode: arithmetic of the residual b - A mu, QAMS_PREC_FF
+                       (default) or QAMS_PREC_FP64 */
 } qams_solve_opts;
 
 typedef struct {

@@ -12,6 +12,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 PREC_FP64 = 0
 PREC_FP32 = 1
+PREC_FF = 2  # float-float pair sum on complex128 data
 
 
 def lib_path() -> str:
@@ -20,7 +21,8 @@ def lib_path() -> str:
 
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int), ("tol", C.c_double),
-                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("precondition", C.c_int)]
+                ("inner_tol", C.c_double), ("max_refine", C.c_int), ("precondition", C.c_int),
+                ("residual", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -232,7 +234,7 @@ class Context:
     def pairsum(self, sigma, y, precision: int = PREC_FP64, stream=None):
         import torch
         R = sigma.shape[1]
-        dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
+        dt = torch.complex64 if precision == PREC_FP32 else torch.complex128
         _check(self.lib.qams_pairsum(self._h, R, _dev(sigma, dt, (self.N, R), "sigma"),
                                      _dev(y, dt, (self.N, R), "y"), precision, C.c_void_p(_stream_ptr(stream))),
                "qams_pairsum")
@@ -265,7 +267,7 @@ class Context:
     def apply(self, x, y, precision: int = PREC_FP64, stream=None):
         import torch
         R = x.shape[1]
-        dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
+        dt = torch.complex64 if precision == PREC_FP32 else torch.complex128
         _check(self.lib.qams_apply(self._h, R, _dev(x, dt, (self.N, R), "x"), _dev(y, dt, (self.N, R), "y"),
                                    precision, C.c_void_p(_stream_ptr(stream))), "qams_apply")
 
@@ -279,14 +281,14 @@ class Context:
 
     def _diag(self, name, x, y, precision, stream):
         import torch
-        dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
+        dt = torch.complex64 if precision == PREC_FP32 else torch.complex128
         R = x.shape[1]
         _check(getattr(self.lib, name)(self._h, R, _dev(x, dt, (self.N, R), "x"), _dev(y, dt, (self.N, R), "y"),
                                        precision, C.c_void_p(_stream_ptr(stream))), name)
 
     def solve(self, rhs, mu, precision: int = PREC_FP32, tol: float = None, restart: int = None,
               max_iters: int = None, inner_tol: float = None, precondition: bool = True, stream=None,
-              check: bool = True):
+              check: bool = True, residual: int = None):
         """Solve A mu = rhs; returns a dict of solver statistics."""
         import torch
         R = rhs.shape[1]
@@ -304,6 +306,8 @@ class Context:
         if inner_tol is not None:
             o.inner_tol = inner_tol
         o.precondition = 1 if precondition else 0
+        if residual is not None:
+            o.residual = residual
         st = SolveStats()
         code = self.lib.qams_solve(self._h, R, _dev(rhs, torch.complex128, (self.N, R), "rhs"),
                                    _dev(mu, torch.complex128, (self.N, R), "mu"), C.byref(o), C.byref(st),

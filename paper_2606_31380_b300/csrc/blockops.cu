@@ -153,7 +153,7 @@ int qams_apply_launch(qams_ctx* c, int R, const void* x, void* y, int precision,
     if (rc) return rc;
   }
   const long long n = c->N * R;
-  if (precision == QAMS_PREC_FP64) {
+  if (precision != QAMS_PREC_FP32) {
     weight_kernel<double2, qd4><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
         (const qd4*)c->x64.p, (const double2*)x, (double2*)c->ws_sigma.p, c->N, R);
   } else {
@@ -164,5 +164,5 @@ int qams_apply_launch(qams_ctx* c, int R, const void* x, void* y, int precision,
   QAMS_CUDA(cudaGetLastError());
   int rc = qams_pairsum_launch(c, R, c->ws_sigma.p, y, precision, st);
   if (rc) return rc;
-  return qams_block_apply(c, R, x, y, precision, true, st);
+  return qams_block_apply(c, R, x, y, precision == QAMS_PREC_FF ? QAMS_PREC_FP64 : precision, true, st);
 }

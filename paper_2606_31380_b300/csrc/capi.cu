@@ -36,7 +36,7 @@ void qams_dev_free(qams_ctx* c, DeviceBuf* b) {
 
 qams_ctx::~qams_ctx() {
   cudaSetDevice(device);
-  for (DeviceBuf* b : {&x64, &n64, &x32, &n32, &centers, &boff, &jac64, &d_tiles, &d_splits, &partial,
+  for (DeviceBuf* b : {&x64, &n64, &x32, &n32, &x32lo, &n32lo, &centers, &boff, &jac64, &d_tiles, &d_splits, &partial,
                         &blocks64, &blocks32, &blk_off, &ws_sigma, &ws_y, &pinv32, &pinv64})
     qams_dev_free(this, b);
 }
@@ -95,7 +95,7 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
       if (std::sqrt(dx * dx + dy * dy + dz * dz) < rad[i] + rad[j] + min_gap) return QAMS_EGEOM;
     }
   QAMS_CUDA(cudaSetDevice(c->device));
-  for (DeviceBuf* b : {&c->x64, &c->n64, &c->x32, &c->n32, &c->centers, &c->boff, &c->jac64, &c->blocks64,
+  for (DeviceBuf* b : {&c->x64, &c->n64, &c->x32, &c->n32, &c->x32lo, &c->n32lo, &c->centers, &c->boff, &c->jac64, &c->blocks64,
                        &c->blocks32, &c->blk_off, &c->ws_sigma, &c->ws_y, &c->pinv32, &c->pinv64})
     qams_dev_free(c, b);
   c->assembled = false;
@@ -106,7 +106,7 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
   const long long N = c->N;
   const int nb = n_bodies;
   std::vector<double> x4(4 * N), n4(4 * N), cen(4 * nb);
-  std::vector<float> xl(4 * N), nl(4 * N);
+  std::vector<float> xl(4 * N), nl(4 * N), xlo(4 * N, 0.0f), nlo(4 * N, 0.0f);
   std::vector<long long> off(nb + 1);
   for (int b = 0; b < nb; ++b) {
     const BodyHost& B = c->bodies[b];
@@ -117,8 +117,11 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
       for (int r = 0; r < 3; ++r) {
         x4[4 * t + r] = c->hx[3 * t + r];
         n4[4 * t + r] = c->hn[3 * t + r];
-        xl[4 * t + r] = (float)(c->hx[3 * t + r] - B.d.center[r]);
+        const double xr = c->hx[3 * t + r] - B.d.center[r];
+        xl[4 * t + r] = (float)xr;
         nl[4 * t + r] = (float)c->hn[3 * t + r];
+        xlo[4 * t + r] = (float)(xr - (double)xl[4 * t + r]);
+        nlo[4 * t + r] = (float)(c->hn[3 * t + r] - (double)nl[4 * t + r]);
       }
       x4[4 * t + 3] = c->hw[t];
       n4[4 * t + 3] = 0.0;
@@ -131,6 +134,8 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
   if ((rc = qams_dev_alloc(c, &c->n64, sizeof(double) * 4 * N))) return rc;
   if ((rc = qams_dev_alloc(c, &c->x32, sizeof(float) * 4 * N))) return rc;
   if ((rc = qams_dev_alloc(c, &c->n32, sizeof(float) * 4 * N))) return rc;
+  if ((rc = qams_dev_alloc(c, &c->x32lo, sizeof(float) * 4 * N))) return rc;
+  if ((rc = qams_dev_alloc(c, &c->n32lo, sizeof(float) * 4 * N))) return rc;
   if ((rc = qams_dev_alloc(c, &c->centers, sizeof(double) * 4 * nb))) return rc;
   if ((rc = qams_dev_alloc(c, &c->boff, sizeof(long long) * (nb + 1)))) return rc;
   if ((rc = qams_dev_alloc(c, &c->jac64, sizeof(double) * N))) return rc;
@@ -143,6 +148,8 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
   QAMS_CUDA(cudaMemcpy(c->n64.p, n4.data(), sizeof(double) * 4 * N, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->x32.p, xl.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->n32.p, nl.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->x32lo.p, xlo.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->n32lo.p, nlo.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->centers.p, cen.data(), sizeof(double) * 4 * nb, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->boff.p, off.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice));
   return qams_pairsum_prepare(c);
@@ -179,7 +186,7 @@ int qams_set_wavenumber(qams_ctx* c, double k, double eta) {
 
 int qams_pairsum(qams_ctx* c, int R, const void* sigma, void* y, int precision, void* stream) {
   if (!c || R < 1 || !sigma || !y || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
-  if (precision != QAMS_PREC_FP64 && precision != QAMS_PREC_FP32) return QAMS_EINVAL;
+  if (precision != QAMS_PREC_FP64 && precision != QAMS_PREC_FP32 && precision != QAMS_PREC_FF) return QAMS_EINVAL;
   QAMS_CUDA(cudaSetDevice(c->device));
   return qams_pairsum_launch(c, R, sigma, y, precision, (cudaStream_t)stream);
 }
@@ -238,7 +245,7 @@ int qams_copy_preconditioner(const qams_ctx* c, int body, void* dst, void* strea
 
 int qams_apply(qams_ctx* c, int R, const void* x, void* y, int precision, void* stream) {
   if (!c || R < 1 || !x || !y || !c->assembled) return QAMS_EINVAL;
-  if (precision != QAMS_PREC_FP64 && precision != QAMS_PREC_FP32) return QAMS_EINVAL;
+  if (precision != QAMS_PREC_FP64 && precision != QAMS_PREC_FP32 && precision != QAMS_PREC_FF) return QAMS_EINVAL;
   QAMS_CUDA(cudaSetDevice(c->device));
   return qams_apply_launch(c, R, x, y, precision, (cudaStream_t)stream);
 }

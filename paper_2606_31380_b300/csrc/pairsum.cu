@@ -16,6 +16,7 @@
 // part e^{ik rho0} is applied once per (target, source body) in FP64.
 #include <cmath>
 
+#include "ffloat.cuh"
 #include "phase.cuh"
 #include "qams_internal.h"
 
@@ -197,6 +198,132 @@ __global__ void __launch_bounds__(TILE) pairsum_f64_kernel(
   }
 }
 
+// Float-float path (FP64-accurate result from FP32 arithmetic, ~48 bits):
+// the same body-local decomposition as the FP32 path,
+//   rho^2 = rho0^2 + e,  e = 2 dc.d + |d|^2,  rho - rho0 = e/(rho + rho0),
+// with every per-pair quantity in float-float.  The body-pair constants
+// (dc, rho0, dc.x~_t, dc.y~_s, n_s.dc) are formed in FP64 once per target or
+// per staged source; the per-pair work has no FP64 instruction.  Partial sums
+// go to FP64 every CHUNK sources, and e^{ik rho0} is applied in FP64 per
+// source body.  sigma and the result are complex128.
+template <int RC>
+__global__ void __launch_bounds__(TILE) pairsum_ff_kernel(
+    const TargetTile* __restrict__ tiles, const SourceSplit* __restrict__ splits,
+    const long long* __restrict__ boff, const qd4* __restrict__ centers, const float4* __restrict__ xhi,
+    const float4* __restrict__ xlo, const float4* __restrict__ nhi, const float4* __restrict__ nlo,
+    const double2* __restrict__ sigma, int R, int r0, double k, double eta, double2* __restrict__ out,
+    long long split_stride, int out_ld, int out_r0) {
+  __shared__ float4 sph[CHUNK], spl[CHUNK];  // y~_s (hi / lo), .w = dc.y~_s (hi / lo)
+  __shared__ float4 snh[CHUNK], snl[CHUNK];  // n_s (hi / lo), .w = n_s.dc (hi / lo)
+  __shared__ float4 ssg[CHUNK][RC];          // sigma: re hi, re lo, im hi, im lo
+  __shared__ float4 tab[256];
+
+  ff_phase_table_fill(tab);
+  const TargetTile tile = tiles[blockIdx.x];
+  const SourceSplit split = splits[blockIdx.y];
+  const int tid = threadIdx.x;
+  const bool active = tid < tile.count;
+  const long long t = tile.start + (active ? tid : 0);
+  const float4 th = xhi[t], tl = xlo[t];
+  const ff xtx{th.x, tl.x}, xty{th.y, tl.y}, xtz{th.z, tl.z};
+  const qd4 ca = centers[tile.body];
+  const ff kf = ff_from_double(k);
+  const ff etaf = ff_from_double(eta);
+
+  double2 tot[RC];
+#pragma unroll
+  for (int r = 0; r < RC; ++r) tot[r] = make_double2(0.0, 0.0);
+
+  for (int b = split.begin; b < split.end; ++b) {
+    if (b == tile.body) continue;
+    const qd4 cb = centers[b];
+    const double dcx = ca.x - cb.x, dcy = ca.y - cb.y, dcz = ca.z - cb.z;
+    const double rho0 = sqrt(dcx * dcx + dcy * dcy + dcz * dcz);
+    double s0d, c0d;
+    sincos(k * rho0, &s0d, &c0d);
+    const ff r0f = ff_from_double(rho0);
+    const ff r02 = ff_from_double(rho0 * rho0);
+    const ff At = ff_from_double(dcx * ((double)th.x + tl.x) + dcy * ((double)th.y + tl.y) +
+                                 dcz * ((double)th.z + tl.z));
+
+    double2 bacc[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) bacc[r] = make_double2(0.0, 0.0);
+
+    const long long send = boff[b + 1];
+    for (long long s0 = boff[b]; s0 < send; s0 += CHUNK) {
+      __syncthreads();
+      const long long i = s0 + tid;
+      if (i < send) {
+        const float4 ph = xhi[i], pl = xlo[i], qh = nhi[i], ql = nlo[i];
+        const double yx = (double)ph.x + pl.x, yy = (double)ph.y + pl.y, yz = (double)ph.z + pl.z;
+        const double nx = (double)qh.x + ql.x, ny = (double)qh.y + ql.y, nz = (double)qh.z + ql.z;
+        const ff bs = ff_from_double(dcx * yx + dcy * yy + dcz * yz);
+        const ff ns = ff_from_double(nx * dcx + ny * dcy + nz * dcz);
+        sph[tid] = make_float4(ph.x, ph.y, ph.z, bs.hi);
+        spl[tid] = make_float4(pl.x, pl.y, pl.z, bs.lo);
+        snh[tid] = make_float4(qh.x, qh.y, qh.z, ns.hi);
+        snl[tid] = make_float4(ql.x, ql.y, ql.z, ns.lo);
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+          const double2 v = sigma[i * R + r0 + r];
+          const ff re = ff_from_double(v.x), im = ff_from_double(v.y);
+          ssg[tid][r] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+      }
+      __syncthreads();
+      const int cnt = (int)min((long long)CHUNK, send - s0);
+      ff ar[RC], ai[RC];
+#pragma unroll
+      for (int r = 0; r < RC; ++r) ar[r] = ai[r] = ff{0.0f, 0.0f};
+      for (int j = 0; j < cnt; ++j) {
+        const float4 ph = sph[j], pl = spl[j], qh = snh[j], ql = snl[j];
+        const ff dx = ff_sub(xtx, ff{ph.x, pl.x});
+        const ff dy = ff_sub(xty, ff{ph.y, pl.y});
+        const ff dz = ff_sub(xtz, ff{ph.z, pl.z});
+        const ff dd = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+        const ff e = ff_add(ff_mul_f(ff_sub(At, ff{ph.w, pl.w}), 2.0f), dd);
+        const ff rho = ff_sqrt(ff_add(r02, e));
+        const ff rinv = ff_rcp(rho);
+        const ff delta = ff_div(e, ff_add(rho, r0f));
+        ff sn, cs;
+        ff_sincos(ff_mul(kf, delta), tab, &sn, &cs);
+        // n_s.(y_s - x_t) = -(n_s.dc + n_s.d)
+        const ff nd = ff_add(ff_add(ff_mul(ff{qh.x, ql.x}, dx), ff_mul(ff{qh.y, ql.y}, dy)),
+                             ff_add(ff_mul(ff{qh.z, ql.z}, dz), ff{qh.w, ql.w}));
+        const ff rinv2 = ff_mul(rinv, rinv);
+        const ff are = ff_mul(nd, rinv2);                                  // -nyx / rho^2 with nyx = -nd
+        const ff aim = ff_sub(ff_mul(ff_mul(kf, ff_neg(nd)), rinv), etaf);  // k nyx / rho - eta
+        const ff kre = ff_mul(ff_sub(ff_mul(cs, are), ff_mul(sn, aim)), rinv);
+        const ff kim = ff_mul(ff_add(ff_mul(sn, are), ff_mul(cs, aim)), rinv);
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+          const float4 sg = ssg[j][r];
+          const ff sre{sg.x, sg.y}, sim{sg.z, sg.w};
+          ar[r] = ff_add(ar[r], ff_sub(ff_mul(kre, sre), ff_mul(kim, sim)));
+          ai[r] = ff_add(ai[r], ff_add(ff_mul(kre, sim), ff_mul(kim, sre)));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RC; ++r) {
+        bacc[r].x += ff_to_double(ar[r]);
+        bacc[r].y += ff_to_double(ai[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+      tot[r].x += c0d * bacc[r].x - s0d * bacc[r].y;
+      tot[r].y += c0d * bacc[r].y + s0d * bacc[r].x;
+    }
+  }
+  if (active) {
+    const double inv4pi = 0.079577471545947667884;
+    double2* o = out + split_stride * blockIdx.y + t * out_ld + out_r0;
+#pragma unroll
+    for (int r = 0; r < RC; ++r) o[r] = make_double2(tot[r].x * inv4pi, tot[r].y * inv4pi);
+  }
+}
+
 // y[t][r0 + r] = sum over splits of part[split][t][r], r < rc (fixed order)
 template <typename C>
 __global__ void reduce_splits_kernel(const C* __restrict__ part, int S, long long N, int rc, C* __restrict__ y,
@@ -237,6 +364,15 @@ void launch_f64(qams_ctx* c, dim3 grid, const double2* sigma, int R, int r0, dou
   pairsum_f64_kernel<RC><<<grid, TILE, 0, st>>>(
       (const TargetTile*)c->d_tiles.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
       (const qd4*)c->x64.p, (const qd4*)c->n64.p, sigma, R, r0, c->k, c->eta, out, stride, ld, or0); qams_count_launch();
+}
+
+template <int RC>
+void launch_ff(qams_ctx* c, dim3 grid, const double2* sigma, int R, int r0, double2* out, long long stride,
+               int ld, int or0, cudaStream_t st) {
+  pairsum_ff_kernel<RC><<<grid, TILE, 0, st>>>(
+      (const TargetTile*)c->d_tiles.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
+      (const qd4*)c->centers.p, (const float4*)c->x32.p, (const float4*)c->x32lo.p, (const float4*)c->n32.p,
+      (const float4*)c->n32lo.p, sigma, R, r0, c->k, c->eta, out, stride, ld, or0); qams_count_launch();
 }
 
 }  // namespace
@@ -312,12 +448,22 @@ int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int prec
       const long long stride = S > 1 ? c->N * rc : 0;
       const int ld = S > 1 ? rc : R, or0 = S > 1 ? 0 : r0;
       const double2* sg = (const double2*)sigma;
-      switch (rc) {
-        case 16: launch_f64<16>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
-        case 8: launch_f64<8>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
-        case 4: launch_f64<4>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
-        case 2: launch_f64<2>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
-        default: launch_f64<1>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+      if (precision == QAMS_PREC_FF) {
+        switch (rc) {
+          case 16: launch_ff<16>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+          case 8: launch_ff<8>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+          case 4: launch_ff<4>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+          case 2: launch_ff<2>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+          default: launch_ff<1>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        }
+      } else {
+        switch (rc) {
+          case 16: launch_f64<16>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+          case 8: launch_f64<8>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+          case 4: launch_f64<4>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+          case 2: launch_f64<2>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+          default: launch_f64<1>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
+        }
       }
       QAMS_CUDA(cudaGetLastError());
       if (S > 1) {

@@ -84,6 +84,8 @@ struct qams_ctx {
   DeviceBuf n64;     // double4 [N]: world normal
   DeviceBuf x32;     // float4  [N]: body-local position x - c_b, w in .w
   DeviceBuf n32;     // float4  [N]: world normal
+  DeviceBuf x32lo;   // float4  [N]: x - c_b - x32 (float-float tails)
+  DeviceBuf n32lo;   // float4  [N]: normal - n32
   DeviceBuf centers; // double4 [nb]
   DeviceBuf boff;    // long long [nb+1]
   DeviceBuf jac64;   // double [N]: |J| at the nodes

@@ -325,6 +325,7 @@ extern "C" int qams_solve(qams_ctx* c, int R, const void* rhs, void* mu, const q
   qams_solve_opts_default(&o);
   if (opts) o = *opts;
   if (o.precision != QAMS_PREC_FP64 && o.precision != QAMS_PREC_FP32) return QAMS_EINVAL;
+  if (o.precision == QAMS_PREC_FP32 && o.residual != QAMS_PREC_FP64 && o.residual != QAMS_PREC_FF) return QAMS_EINVAL;
   if (o.restart < 1 || o.restart > 200 || o.max_iters < 1 || !(o.tol > 0)) return QAMS_EINVAL;
   QAMS_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -375,7 +376,7 @@ extern "C" int qams_solve(qams_ctx* c, int R, const void* rhs, void* mu, const q
           if (irc && irc != QAMS_ENOCONV) { rc = irc; break; }
           if ((rc = S.unprecondition((double2*)dd.p))) break;
           add_kernel<<<nblk(n), 256, 0, st>>>((double2*)xr.p, (const double2*)dd.p, n); qams_count_launch();
-          rc = qams_apply_launch(c, R, xr.p, dd.p, QAMS_PREC_FP64, st);
+          rc = qams_apply_launch(c, R, xr.p, dd.p, o.residual, st);
           ++fp64_applies;
           if (rc) break;
           residual_kernel<<<nblk(n), 256, 0, st>>>((const double2*)rhs, (const double2*)dd.p, (double2*)rr.p, n); qams_count_launch();
@@ -422,5 +423,6 @@ extern "C" void qams_solve_opts_default(qams_solve_opts* o) {
   o->tol = 1e-11;
   o->inner_tol = 1e-5;
   o->max_refine = 12;
+  o->residual = QAMS_PREC_FF;
   o->precondition = 1;
 }

@@ -12,6 +12,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12   # pair-sum parity, FP64 path (apply-level target <= 1e-13 per entry norm)
 FP32_TOL = 3e-5    # FP32 path: FP32 pair arithmetic with per-body-pair phase split
+FF_TOL = 1e-12     # float-float path: ~48-bit pair arithmetic, FP64-accurate by design
 
 
 def _ragged_scene(k=2.5, eta=1.0, n_rhs=1):
@@ -29,7 +30,7 @@ def _ragged_scene(k=2.5, eta=1.0, n_rhs=1):
 def _gpu_pairsum(ctx, sigma, prec):
     import torch
     import paper_2606_31380_b300 as q
-    dt = torch.complex128 if prec == q.PREC_FP64 else torch.complex64
+    dt = torch.complex64 if prec == q.PREC_FP32 else torch.complex128
     s = torch.from_numpy(sigma).to(dt).cuda()
     y = torch.full_like(s, float("nan"))
     ctx.pairsum(s, y, prec)
@@ -57,6 +58,7 @@ def test_pairsum_ragged_fp64_and_fp32(n_rhs):
     ref = op.pair_sum(nodes, sigma, sc.k, sc.eta)
     assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FP64), ref) < FP64_TOL
     assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FP32), ref) < FP32_TOL
+    assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FF), ref) < FF_TOL
 
 
 @pytest.mark.parametrize("eta,k", [(0.0, 1.0), (1.0, 15.0)])
@@ -69,6 +71,7 @@ def test_pairsum_small_random_scene(eta, k):
     ref = op.pair_sum(nodes, sigma, sc.k, sc.eta)
     assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FP64), ref) < FP64_TOL
     assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FP32), ref) < FP32_TOL
+    assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FF), ref) < FF_TOL
 
 
 @pytest.mark.parametrize("cfg", [1, 2])
@@ -87,6 +90,7 @@ def test_pairsum_full_size_sampled_rows(cfg):
     ref = op.pair_sum(nodes, sigma, sc.k, sc.eta, targets=rows)
     assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FP64)[rows], ref) < FP64_TOL
     assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FP32)[rows], ref) < FP32_TOL
+    assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FF)[rows], ref) < FF_TOL
 
 
 def test_incident_and_farfield():
@@ -116,6 +120,7 @@ def test_pairsum_thousand_bodies_fp32_sampled_rows():
     rows = np.concatenate([[0, ctx.N - 1], rng.integers(0, ctx.N, 14)])
     ref = op.pair_sum(nodes, sigma, sc.k, sc.eta, targets=rows)
     assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FP32)[rows], ref) < FP32_TOL
+    assert rel_err(_gpu_pairsum(ctx, sigma, q.PREC_FF)[rows], ref) < FF_TOL
 
 
 def test_scattered_field_against_oracle():
@@ -155,6 +160,7 @@ def test_pairsum_fp64_large_phases():
     sigma = scenes.rhs_seeded(ctx.N, 2, 13)
     ref = op.pair_sum(nodes, sigma, sc.k, sc.eta)
     got = _gpu_pairsum(ctx, sigma, q.PREC_FP64)
+    gff = _gpu_pairsum(ctx, sigma, q.PREC_FF)
     # each body's rows separately: their scales differ by the distances.  Both
     # sides round rho differently by ~1 ulp, i.e. k rho by ~2e-13 at these
     # distances, which sets the tolerance; a wrong table entry, index or
@@ -163,3 +169,4 @@ def test_pairsum_fp64_large_phases():
     for a in range(len(bodies)):
         rows = slice(off[a], off[a + 1])
         assert rel_err(got[rows], ref[rows]) < FP64_TOL
+        assert rel_err(gff[rows], ref[rows]) < FF_TOL

@@ -119,3 +119,7 @@ def test_apply_full_size_sampled_rows():
     ctx.apply(xd, y, q.PREC_FP64)
     torch.cuda.synchronize()
     assert rel_err(y.cpu().numpy()[rows], ref) < 1e-12
+    # the refinement residual's operator: float-float pair sum, FP64 blocks
+    ctx.apply(xd, y, q.PREC_FF)
+    torch.cuda.synchronize()
+    assert rel_err(y.cpu().numpy()[rows], ref) < 1e-12

@@ -217,3 +217,33 @@ def test_farfield_reciprocity_curved_bodies():
     off = ~np.eye(8, dtype=bool)
     err = np.max(np.abs(U - U[neg][:, neg].T)[off]) / np.max(np.abs(U))
     assert err < 1e-6
+
+
+def test_hundred_bodies_sixteen_rhs_residual_rows():
+    """100 bodies x 1152 nodes, k = 10, 16 incident directions (N = 115,200):
+    the mixed solve of all 16 columns, then sampled rows of b - A mu from
+    oracle self-block rows and explicit pair sums, every column."""
+    import torch
+    import paper_2606_31380_b300 as q
+    from oracle.selfblock import self_block_rows_parallel
+    sc = scenes.config(2)
+    ctx = make_ctx(sc)
+    ctx.assemble()
+    R = sc.n_rhs
+    b = torch.zeros((ctx.N, R), dtype=torch.complex128, device="cuda")
+    ctx.incident_plane(sc.directions, b)
+    mu = torch.zeros_like(b)
+    st = ctx.solve(b, mu, q.PREC_FP32, tol=1e-11)
+    assert st["rel_residual"] <= 1e-11
+    nodes = [body_nodes(x) for x in sc.bodies]
+    off = ctx.body_offsets()
+    m = mu.cpu().numpy()
+    bb = op.incident(nodes, sc.directions, sc.k)
+    w = np.concatenate([n.w for n in nodes])
+    rows = [3, 1152 * 41 + 577, 1152 * 99 + 1151]
+    Am = op.pair_sum(nodes, w[:, None] * m, sc.k, sc.eta, targets=rows)
+    for i, gidx in enumerate(rows):
+        bi = int(np.searchsorted(off, gidx, side="right") - 1)
+        row = self_block_rows_parallel(nodes[bi], [gidx - off[bi]], sc.k, sc.eta, workers=1)[0]
+        Am[i] += row @ m[off[bi]:off[bi + 1]]
+    assert np.max(np.abs(Am - bb[rows])) < 1e-9 * np.max(np.abs(bb))

@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "ffloat.cuh"
 #include "qams_internal.h"
 
 namespace {
@@ -76,6 +77,10 @@ struct alignas(16) RowShared {
   double ctab[4 * MAXM2];  // cos(2 pi j / M), j < M
   double cth[2 * MAXN], sth[2 * MAXN];
   double inv_odd[MAXP + 1];  // 1/(2n - 1)
+  // float-float copies for the accumulation and the panel's inverse DFT
+  float4 dff[2 * MAXN], tff[2 * MAXN];  // theta-coefficients (re hi, re lo, im hi, im lo)
+  float4 csff[2 * MAXN];                // (cos hi, cos lo, sin hi, sin lo)(2 pi j / 2N)
+  float2 plff[MAXORD];                  // outer weight x P_l
 };
 
 struct AsmBody {
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   // so every array stays 16-byte aligned)
   double* bq = reinterpret_cast<double*>(smem_raw + sizeof(RowShared));
   double* bdq = bq + BATCH * pstride;
-  double2* accD = reinterpret_cast<double2*>(bdq + BATCH * pstride);
+  float4* accD = reinterpret_cast<float4*>(bdq + BATCH * pstride);
 
   const long long g = row0 + blockIdx.x;  // global target node
   int lo = 0, hi = nb - 1;
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   const int tid = threadIdx.x;
   const int nth = B.n_theta, N = nth / 2, order = B.order;
   const int per_panel = order * nth;
-  double2* accS = accD + per_panel;
+  float4* accS = accD + per_panel;
   const int nbn = B.n_panels * per_panel;
   const int t = (int)(g - B.offset);
   const int p = t / per_panel;
@@ -437,7 +442,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   const int P = N + n1 + 2;
   double2* row = blocks + B.blk + (long long)t * nbn;
 
-  for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_double2(0.0, 0.0);
+  for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   int n_far = 0;  // thread 0: far outer nodes of this row
   // far-ring contributions in sample space, entries e = tid + q NT of the current panel
   double far_re[MAXE], far_im[MAXE];
@@ -484,7 +489,11 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
     S.s2tab[q] = sv * sv;
   }
   for (int j = tid; j < M; j += NT) S.ctab[j] = cospi(2.0 * j / M);
-  for (int j = tid; j < nth; j += NT) sincospi(2.0 * j / nth, &S.sth[j], &S.cth[j]);
+  for (int j = tid; j < nth; j += NT) {
+    sincospi(2.0 * j / nth, &S.sth[j], &S.cth[j]);
+    const ff cj = ff_from_double(S.cth[j]), sj = ff_from_double(S.sth[j]);
+    S.csff[j] = make_float4(cj.hi, cj.lo, sj.hi, sj.lo);
+  }
   for (int n = tid; n <= MAXP; n += NT) S.inv_odd[n] = 1.0 / (2.0 * n - 1.0);
   __syncthreads();
   const int nq = S.nq;
@@ -517,6 +526,8 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
         for (int mm = 0; mm < order; ++mm)
           if (mm != tid) v *= xs - gl_x[mm];
         S.pl[tid] = v;
+        const ff vf = ff_from_double(v);
+        S.plff[tid] = make_float2(vf.hi, vf.lo);
       }
       if (farn) {
         // far ring: integrands sampled at the azimuthal nodes, times the
@@ -688,20 +699,25 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
           tre_ += fac * (eta * g0i);
           timv += fac * (-eta * g0r);
         }
-        S.dre[mm] = dre_;
-        S.dim_[mm] = dimv;
-        S.tre[mm] = tre_;
-        S.tim[mm] = timv;
+        const ff a = ff_from_double(dre_), b = ff_from_double(dimv);
+        const ff cc = ff_from_double(tre_), d = ff_from_double(timv);
+        S.dff[mm] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        S.tff[mm] = make_float4(cc.hi, cc.lo, d.hi, d.lo);
       }
       __syncthreads();
-      // F: accumulate w P_l(s) x (theta-coefficients) for the node's panel
+      // F: accumulate w P_l(s) x (theta-coefficients) for the node's panel, in
+      // float-float (~48 bits; the FP32 pipe instead of the 64x slower FP64 one)
       for (int e = tid; e < per_panel; e += NT) {
         const int l = e / nth, mm = e % nth;
-        const double f = S.pl[l];
-        accD[e].x += f * S.dre[mm];
-        accD[e].y += f * S.dim_[mm];
-        accS[e].x += f * S.tre[mm];
-        accS[e].y += f * S.tim[mm];
+        const ff f{S.plff[l].x, S.plff[l].y};
+        const float4 dv = S.dff[mm], tv = S.tff[mm];
+        const float4 ad = accD[e], as = accS[e];
+        const ff d0 = ff_add(ff{ad.x, ad.y}, ff_mul(f, ff{dv.x, dv.y}));
+        const ff d1 = ff_add(ff{ad.z, ad.w}, ff_mul(f, ff{dv.z, dv.w}));
+        const ff s0 = ff_add(ff{as.x, as.y}, ff_mul(f, ff{tv.x, tv.y}));
+        const ff s1 = ff_add(ff{as.z, as.w}, ff_mul(f, ff{tv.z, tv.w}));
+        accD[e] = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+        accS[e] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
       }
       __syncthreads();
       }  // modal path
@@ -711,20 +727,22 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
         const int base = ip * per_panel;
         for (int e = tid; e < per_panel; e += NT) {
           const int l = e / nth, j = e % nth;
-          const double J = jac[B.offset + base + e];
-          double sr = 0.0, si = 0.0;
+          const ff J = ff_from_double(jac[B.offset + base + e]);
+          ff sr{0.f, 0.f}, si{0.f, 0.f};
           int idx = 0;
           for (int mm = 0; mm < nth; ++mm) {
             // e^{i m theta_j} with m = mm or mm - 2N (the same value): table[(mm j) mod 2N]
-            const double cr = S.cth[idx], ci = S.sth[idx];
-            const double ar = accD[l * nth + mm].x + J * accS[l * nth + mm].x;
-            const double ai = accD[l * nth + mm].y + J * accS[l * nth + mm].y;
-            sr += ar * cr - ai * ci;
-            si += ar * ci + ai * cr;
+            const float4 cs = S.csff[idx];
+            const float4 ad = accD[l * nth + mm], as = accS[l * nth + mm];
+            const ff cr{cs.x, cs.y}, ci{cs.z, cs.w};
+            const ff ar = ff_add(ff{ad.x, ad.y}, ff_mul(J, ff{as.x, as.y}));
+            const ff ai = ff_add(ff{ad.z, ad.w}, ff_mul(J, ff{as.z, as.w}));
+            sr = ff_add(sr, ff_sub(ff_mul(ar, cr), ff_mul(ai, ci)));
+            si = ff_add(si, ff_add(ff_mul(ar, ci), ff_mul(ai, cr)));
             idx += j;
             if (idx >= nth) idx -= nth;
           }
-          double2 v = make_double2(sr * inv_nth, si * inv_nth);
+          double2 v = make_double2(ff_to_double(sr) * inv_nth, ff_to_double(si) * inv_nth);
           if (base + e == t) v.x += 0.5;
           row[base + e] = v;
         }
@@ -739,7 +757,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
           far_re[qq] = far_im[qq] = 0.0;
         }
         __syncthreads();
-        for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_double2(0.0, 0.0);
+        for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
       }
     }
@@ -766,9 +784,10 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
 
 static_assert(sizeof(RowShared) % 16 == 0, "double2 accumulators follow RowShared");
 
-// Dynamic shared memory of one CTA: RowShared, Q and dQ of a batch, two panel accumulators.
+// Dynamic shared memory of one CTA: RowShared, Q and dQ of a batch, two panel
+// accumulators of float-float complex entries.
 size_t qams_selfblock_smem(int max_per_panel, int pstride) {
-  return sizeof(RowShared) + 2 * sizeof(double) * BATCH * (size_t)pstride + 2 * sizeof(double2) * (size_t)max_per_panel;
+  return sizeof(RowShared) + 2 * sizeof(double) * BATCH * (size_t)pstride + 2 * sizeof(float4) * (size_t)max_per_panel;
 }
 
 int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {

@@ -41,8 +41,8 @@ namespace {
 constexpr int NT = 128;      // threads per CTA
 constexpr int BATCH = 16;    // outer nodes whose recursions run together (warp 0)
 constexpr int MAXP = 96;     // highest static mode N + n1 + 1
-constexpr int MAXM2 = 96;    // M/2 + 1 samples of the smooth factors
-constexpr int MAXN1 = 88;    // highest smooth-factor mode + 2
+constexpr int MAXM2 = 72;    // M/2 + 1 samples of the smooth factors
+constexpr int MAXN1 = 64;    // highest smooth-factor mode + 2 (k r_max up to ~35)
 constexpr int MAXN = 32;     // N = n_theta / 2
 constexpr int MAXORD = 19;
 constexpr int MAXE = (MAXORD * 2 * MAXN + NT - 1) / NT;  // panel entries per thread
@@ -74,13 +74,15 @@ struct alignas(16) RowShared {
   double pl[MAXORD];
   // row constants
   double s2tab[MAXM2];     // sin^2(pi q / M)
-  double ctab[4 * MAXM2];  // cos(2 pi j / M), j < M
+  double ctab[2 * MAXM2];  // cos(2 pi j / M), j < M
   double cth[2 * MAXN], sth[2 * MAXN];
   double inv_odd[MAXP + 1];  // 1/(2n - 1)
   // float-float copies for the accumulation and the panel's inverse DFT
   float4 dff[2 * MAXN], tff[2 * MAXN];  // theta-coefficients (re hi, re lo, im hi, im lo)
   float4 csff[2 * MAXN];                // (cos hi, cos lo, sin hi, sin lo)(2 pi j / 2N)
   float2 plff[MAXORD];                  // outer weight x P_l
+  float2 fcff[2][MAXN1 + 1];            // cos^ and sinc^ coefficients (convolution inputs)
+  float2 sg0ff[MAXP + 1], sdqff[MAXP + 1];  // g^ and Q' scale
 };
 
 struct AsmBody {
@@ -576,8 +578,12 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       // static coefficients: g^_m = Q scale, d_r g^_m = dchi_r Q' scale - g^_m/(2r),
       // d_z g^_m = dchi_z Q' scale -- all from g^ and Q' scale
       for (int m = tid; m <= P; m += NT) {
-        S.sg0[m] = q[m] * scale;
-        S.sdq[m] = dq[m] * scale;
+        const double g0 = q[m] * scale, gd = dq[m] * scale;
+        S.sg0[m] = g0;
+        S.sdq[m] = gd;
+        const ff a = ff_from_double(g0), b = ff_from_double(gd);
+        S.sg0ff[m] = make_float2(a.hi, a.lo);
+        S.sdqff[m] = make_float2(b.hi, b.lo);
       }
       if (!kz) {
         for (int e = tid; e <= M2; e += NT) {
@@ -603,7 +609,12 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
             if (idx >= M) idx -= M;
             sum += f[qq] * S.ctab[idx];
           }
-          S.fc[fn][n] = twopi_M * (f[0] + ((n & 1) ? -f[M2] : f[M2]) + 2.0 * sum);
+          const double fcv = twopi_M * (f[0] + ((n & 1) ? -f[M2] : f[M2]) + 2.0 * sum);
+          S.fc[fn][n] = fcv;
+          if (fn < 2) {
+            const ff a = ff_from_double(fcv);
+            S.fcff[fn][n] = make_float2(a.hi, a.lo);
+          }
         }
         __syncthreads();
         // C2: spectra of the smooth imaginary parts (multiplying by cos(phi) averages neighbours)
@@ -619,14 +630,18 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
         //   C_m = sum_n sinc^_n g^_{m-n}   (m = 0..N+1; C also at N+2),
         // because d_r g^ and d_z g^ are combinations of g^ and Q' scale, and the
         // sinc-weighted terms are C_m and its cos(phi)-shift (C_{m-1} + C_{m+1})/2.
+        // (in float-float: these are sums of FP64-computed products, ~48 bits suffice)
         const int L0 = N + 2;
         for (int e = tid; e < 3 * L0 + 1; e += NT) {
-          const double* f = e < 2 * L0 ? S.fc[0] : S.fc[1];
-          const double* g = (e >= L0 && e < 2 * L0) ? S.sdq : S.sg0;
+          const float2* f = e < 2 * L0 ? S.fcff[0] : S.fcff[1];
+          const float2* g = (e >= L0 && e < 2 * L0) ? S.sdqff : S.sg0ff;
           const int m = e < L0 ? e : (e < 2 * L0 ? e - L0 : e - 2 * L0);
-          double sum = f[0] * g[m];
-          for (int n = 1; n <= n1; ++n) sum += f[n] * g[abs(m - n)] + f[n] * g[m + n];
-          (e < L0 ? S.cA : (e < 2 * L0 ? S.cB : S.cC))[m] = sum;
+          ff sum = ff_mul(ff{f[0].x, f[0].y}, ff{g[m].x, g[m].y});
+          for (int n = 1; n <= n1; ++n) {
+            const float2 ga = g[abs(m - n)], gb = g[m + n];
+            sum = ff_add(sum, ff_mul(ff{f[n].x, f[n].y}, ff_add(ff{ga.x, ga.y}, ff{gb.x, gb.y})));
+          }
+          (e < L0 ? S.cA : (e < 2 * L0 ? S.cB : S.cC))[m] = ff_to_double(sum);
         }
         __syncthreads();
       }
@@ -865,7 +880,7 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
     const double rmax = bh.rmax;
     A.n1 = (int)std::ceil(1.3 * c->k * rmax + 16.0);
     A.M = 2 * (A.n1 + 8);
-    if (A.n1 + 2 > MAXN1 || A.M / 2 + 1 > MAXM2 || d.n_theta / 2 + A.n1 + 2 > MAXP || 2 * A.M > 4 * MAXM2)
+    if (A.n1 + 2 > MAXN1 || A.M / 2 + 1 > MAXM2 || d.n_theta / 2 + A.n1 + 2 > MAXP || A.M > 2 * MAXM2)
       return QAMS_EINVAL;
     A.rule = rule_off[d.order];
     max_nb = std::max(max_nb, d.order * d.n_theta);

@@ -62,7 +62,7 @@ struct alignas(16) RowShared {
   int bflush[BATCH];            // 1 on the last outer node of a panel
   // per-node work arrays
   double sg0[MAXP + 1], sdq[MAXP + 1];  // static g^ and Q'(chi) scale (modes 0..P)
-  double fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho)
+  float2 fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho) (float-float)
   double fc[3][MAXN1 + 1];      // their cosine coefficients
   double pr[MAXN1 + 1], pz[MAXN1 + 1], f2[MAXN1 + 1];
   double cA[MAXN + 2], cB[MAXN + 2], cC[MAXN + 3];  // the three phi-convolutions (see stage D)
@@ -74,7 +74,7 @@ struct alignas(16) RowShared {
   double pl[MAXORD];
   // row constants
   double s2tab[MAXM2];     // sin^2(pi q / M)
-  double ctab[2 * MAXM2];  // cos(2 pi j / M), j < M
+  float2 ctab[2 * MAXM2];  // cos(2 pi j / M), j < M (float-float)
   double cth[2 * MAXN], sth[2 * MAXN];
   double inv_odd[MAXP + 1];  // 1/(2n - 1)
   // float-float copies for the accumulation and the panel's inverse DFT
@@ -490,7 +490,10 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
     const double sv = sinpi((double)q / M);
     S.s2tab[q] = sv * sv;
   }
-  for (int j = tid; j < M; j += NT) S.ctab[j] = cospi(2.0 * j / M);
+  for (int j = tid; j < M; j += NT) {
+    const ff cj = ff_from_double(cospi(2.0 * j / M));
+    S.ctab[j] = make_float2(cj.hi, cj.lo);
+  }
   for (int j = tid; j < nth; j += NT) {
     sincospi(2.0 * j / nth, &S.sth[j], &S.cth[j]);
     const ff cj = ff_from_double(S.cth[j]), sj = ff_from_double(S.sth[j]);
@@ -588,7 +591,12 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       if (!kz) {
         for (int e = tid; e <= M2; e += NT) {
           const double rho = sqrt(dr * dr + c * c + 4.0 * r * rt * S.s2tab[e]);
-          smooth_factors(k * rho, &S.fs[0][e], &S.fs[1][e], &S.fs[2][e]);
+          double f0, f1, f2v;
+          smooth_factors(k * rho, &f0, &f1, &f2v);
+          const ff a = ff_from_double(f0), b = ff_from_double(f1), cc = ff_from_double(f2v);
+          S.fs[0][e] = make_float2(a.hi, a.lo);
+          S.fs[1][e] = make_float2(b.hi, b.lo);
+          S.fs[2][e] = make_float2(cc.hi, cc.lo);
         }
       }
       // e^{i m alpha} = e^{i 8 l alpha} e^{i j alpha}, m = 8 l + j: 13 sincos, combined in D2
@@ -599,17 +607,20 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       __syncthreads();
       if (!kz) {
         // C1: cosine coefficients f^_n = (2pi/M)[f_0 + (-1)^n f_{M/2} + 2 sum f_q cos(2 pi n q/M)]
+        // (float-float: a sum of M/2 FP64-accurate samples times table cosines)
         for (int e = tid; e < 3 * (n1 + 2); e += NT) {
           const int fn = e / (n1 + 2), n = e % (n1 + 2);
-          const double* f = S.fs[fn];
-          double sum = 0.0;
+          const float2* f = S.fs[fn];
+          ff sum{0.f, 0.f};
           int idx = 0;
           for (int qq = 1; qq < M2; ++qq) {
             idx += n;
             if (idx >= M) idx -= M;
-            sum += f[qq] * S.ctab[idx];
+            sum = ff_add(sum, ff_mul(ff{f[qq].x, f[qq].y}, ff{S.ctab[idx].x, S.ctab[idx].y}));
           }
-          const double fcv = twopi_M * (f[0] + ((n & 1) ? -f[M2] : f[M2]) + 2.0 * sum);
+          const ff fend{(n & 1) ? -f[M2].x : f[M2].x, (n & 1) ? -f[M2].y : f[M2].y};
+          const ff tot = ff_add(ff_add(ff{f[0].x, f[0].y}, fend), ff_mul_f(sum, 2.0f));
+          const double fcv = twopi_M * ff_to_double(tot);
           S.fc[fn][n] = fcv;
           if (fn < 2) {
             const ff a = ff_from_double(fcv);

@@ -66,8 +66,8 @@ struct alignas(16) RowShared {
   double fc[3][MAXN1 + 1];      // their cosine coefficients
   double pr[MAXN1 + 1], pz[MAXN1 + 1], f2[MAXN1 + 1];
   double cA[MAXN + 2], cB[MAXN + 2], cC[MAXN + 3];  // the three phi-convolutions (see stage D)
-  double gre[3][MAXN + 2], gim[3][MAXN + 2];  // G^, d_r G^, d_z G^ (phi coefficients, m <= N+1)
-  double cma[MAXN + 2], sma[MAXN + 2];         // cos(m alpha), sin(m alpha)
+  float4 gff[3][MAXN + 2];  // G^, d_r G^, d_z G^ (phi coefficients, m <= N+1): re hi, re lo, im hi, im lo
+  float4 eff[MAXN + 2];     // (cos hi, cos lo, sin hi, sin lo)(m alpha)
   double ecs[8 + (MAXN + 9) / 8], esn[8 + (MAXN + 9) / 8];  // cos/sin(j alpha), j < 8, then of 8 l alpha
   double dre[2 * MAXN], dim_[2 * MAXN];        // theta-coefficients of the double-layer integrand
   double tre[2 * MAXN], tim[2 * MAXN];         // theta-coefficients of the single-layer integrand
@@ -345,6 +345,20 @@ __device__ void smooth_kernel(const qd4& x, const qd4& y, const qd4& n, double k
   const double f = rinv * 0.079577471545947667884;
   *kre = (cs * are - sn * aim) * f;
   *kim = (sn * are + cs * aim) * f;
+}
+
+// complex float-float helpers
+struct ffc {
+  ff re, im;
+};
+__device__ __forceinline__ ffc ffc_load(float4 v) { return {ff{v.x, v.y}, ff{v.z, v.w}}; }
+__device__ __forceinline__ ffc ffc_mul(ffc a, ffc b) {
+  return {ff_sub(ff_mul(a.re, b.re), ff_mul(a.im, b.im)), ff_add(ff_mul(a.re, b.im), ff_mul(a.im, b.re))};
+}
+// e^{-i m alpha} from (cos, sin)(|m| alpha): cos - i sin for m >= 0, cos + i sin otherwise
+__device__ __forceinline__ ffc ephase(float4 cs, bool nonneg) {
+  const ff c{cs.x, cs.y}, sn{cs.z, cs.w};
+  return {c, nonneg ? ff_neg(sn) : sn};
 }
 
 // Rule tables of one order (see qams_assemble_launch for the layout).
@@ -659,8 +673,9 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       // D2: modal coefficients of G, d_r G, d_z G for m = 0..N+1, and cos/sin(m alpha)
       for (int m = tid; m <= N + 1; m += NT) {
         const int l = 8 + (m >> 3), j = m & 7;
-        S.cma[m] = S.ecs[l] * S.ecs[j] - S.esn[l] * S.esn[j];
-        S.sma[m] = S.esn[l] * S.ecs[j] + S.ecs[l] * S.esn[j];
+        const ff cm = ff_from_double(S.ecs[l] * S.ecs[j] - S.esn[l] * S.esn[j]);
+        const ff sm = ff_from_double(S.esn[l] * S.ecs[j] + S.ecs[l] * S.esn[j]);
+        S.eff[m] = make_float4(cm.hi, cm.lo, sm.hi, sm.lo);
       }
       {
         const double inv2r = 0.5 / r, k2 = k * k;
@@ -680,8 +695,8 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
             re = (dchi_z * S.cB[m] + k2 * c * S.cC[m]) * INV_2PI;
             im = m <= n1 ? S.pz[m] : 0.0;
           }
-          S.gre[comp][m] = re;
-          S.gim[comp][m] = im;
+          const ff a = ff_from_double(re), b = ff_from_double(im);
+          S.gff[comp][m] = make_float4(a.hi, a.lo, b.hi, b.lo);
         }
       }
       __syncthreads();
@@ -691,44 +706,46 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       //   single layer  -i eta G,
       // with K(theta - alpha) -> k^_|m| e^{-i m alpha}; cos(theta) averages m -+ 1 and
       // sin(theta) gives (k_{m-1} - k_{m+1})/(2i).
-      const double na0 = sc[9], na1 = sc[10], nb0 = sc[11], nb1 = sc[12], nb2 = sc[13];
-      const bool zshift = (nb1 != 0.0) || (nb2 != 0.0);
+      // (in float-float: complex products of FP64-computed coefficients)
+      const ff na0 = ff_from_double(sc[9]), na1 = ff_from_double(sc[10]), nb0 = ff_from_double(sc[11]);
+      const ff nb1h = ff_from_double(0.5 * sc[12]), nb2h = ff_from_double(0.5 * sc[13]);
+      const ff etaf = ff_from_double(eta);
+      const bool zshift = (sc[12] != 0.0) || (sc[13] != 0.0);
       for (int mm = tid; mm < nth; mm += NT) {
         const int m0 = mm <= N ? mm : mm - nth;
         const int nsum = (m0 == N) ? 2 : 1;
-        const double fac = (nsum == 2) ? 0.5 : 1.0;
-        double dre_ = 0.0, dimv = 0.0, tre_ = 0.0, timv = 0.0;
+        const float fac = (nsum == 2) ? 0.5f : 1.0f;
+        ffc dsum{{0.f, 0.f}, {0.f, 0.f}}, g0sum{{0.f, 0.f}, {0.f, 0.f}};
         for (int sgn = 0; sgn < nsum; ++sgn) {
           const int m = (sgn == 0) ? m0 : -N;
           const int a0 = abs(m), am1 = abs(m - 1), ap1 = abs(m + 1);
           // e^{-i mv alpha} = cos(|mv| alpha) -/+ i sin(|mv| alpha)
-          const double c0r = S.cma[a0], c0i = m >= 0 ? -S.sma[a0] : S.sma[a0];
-          const double cmr = S.cma[am1], cmi = (m - 1) >= 0 ? -S.sma[am1] : S.sma[am1];
-          const double cpr = S.cma[ap1], cpi = (m + 1) >= 0 ? -S.sma[ap1] : S.sma[ap1];
-          const double krr = S.gre[1][a0] * c0r - S.gim[1][a0] * c0i, kri = S.gre[1][a0] * c0i + S.gim[1][a0] * c0r;
-          const double kzr = S.gre[2][a0] * c0r - S.gim[2][a0] * c0i, kzi = S.gre[2][a0] * c0i + S.gim[2][a0] * c0r;
-          const double g0r = S.gre[0][a0] * c0r - S.gim[0][a0] * c0i, g0i = S.gre[0][a0] * c0i + S.gim[0][a0] * c0r;
-          const double kmr = S.gre[1][am1] * cmr - S.gim[1][am1] * cmi, kmi = S.gre[1][am1] * cmi + S.gim[1][am1] * cmr;
-          const double kpr = S.gre[1][ap1] * cpr - S.gim[1][ap1] * cpi, kpi = S.gre[1][ap1] * cpi + S.gim[1][ap1] * cpr;
-          const double kcr = 0.5 * (kmr + kpr), kci = 0.5 * (kmi + kpi);  // (K^r cos theta)^_m
-          double zr = na0 * krr + na1 * kcr + nb0 * kzr;
-          double zi = na0 * kri + na1 * kci + nb0 * kzi;
+          const ffc c0 = ephase(S.eff[a0], m >= 0), cm = ephase(S.eff[am1], m - 1 >= 0),
+                    cp = ephase(S.eff[ap1], m + 1 >= 0);
+          const ffc kr = ffc_mul(ffc_load(S.gff[1][a0]), c0);
+          const ffc kz = ffc_mul(ffc_load(S.gff[2][a0]), c0);
+          const ffc g0 = ffc_mul(ffc_load(S.gff[0][a0]), c0);
+          const ffc km = ffc_mul(ffc_load(S.gff[1][am1]), cm);
+          const ffc kp = ffc_mul(ffc_load(S.gff[1][ap1]), cp);
+          const ffc kc{ff_mul_f(ff_add(km.re, kp.re), 0.5f), ff_mul_f(ff_add(km.im, kp.im), 0.5f)};  // (K^r cos)^_m
+          ffc z{ff_add(ff_add(ff_mul(na0, kr.re), ff_mul(na1, kc.re)), ff_mul(nb0, kz.re)),
+                ff_add(ff_add(ff_mul(na0, kr.im), ff_mul(na1, kc.im)), ff_mul(nb0, kz.im))};
           if (zshift) {
-            const double zmr = S.gre[2][am1] * cmr - S.gim[2][am1] * cmi, zmi = S.gre[2][am1] * cmi + S.gim[2][am1] * cmr;
-            const double zpr = S.gre[2][ap1] * cpr - S.gim[2][ap1] * cpi, zpi = S.gre[2][ap1] * cpi + S.gim[2][ap1] * cpr;
+            const ffc zm = ffc_mul(ffc_load(S.gff[2][am1]), cm);
+            const ffc zp = ffc_mul(ffc_load(S.gff[2][ap1]), cp);
             // cos: (z_{m-1} + z_{m+1})/2;  sin: -i (z_{m-1} - z_{m+1})/2
-            zr += nb1 * 0.5 * (zmr + zpr) + nb2 * 0.5 * (zmi - zpi);
-            zi += nb1 * 0.5 * (zmi + zpi) - nb2 * 0.5 * (zmr - zpr);
+            z.re = ff_add(z.re, ff_add(ff_mul(nb1h, ff_add(zm.re, zp.re)), ff_mul(nb2h, ff_sub(zm.im, zp.im))));
+            z.im = ff_add(z.im, ff_sub(ff_mul(nb1h, ff_add(zm.im, zp.im)), ff_mul(nb2h, ff_sub(zm.re, zp.re))));
           }
-          dre_ += fac * zr;
-          dimv += fac * zi;
-          tre_ += fac * (eta * g0i);
-          timv += fac * (-eta * g0r);
+          dsum.re = ff_add(dsum.re, ff_mul_f(z.re, fac));
+          dsum.im = ff_add(dsum.im, ff_mul_f(z.im, fac));
+          g0sum.re = ff_add(g0sum.re, ff_mul_f(g0.re, fac));
+          g0sum.im = ff_add(g0sum.im, ff_mul_f(g0.im, fac));
         }
-        const ff a = ff_from_double(dre_), b = ff_from_double(dimv);
-        const ff cc = ff_from_double(tre_), d = ff_from_double(timv);
-        S.dff[mm] = make_float4(a.hi, a.lo, b.hi, b.lo);
-        S.tff[mm] = make_float4(cc.hi, cc.lo, d.hi, d.lo);
+        // single layer -i eta G
+        const ff tre = ff_mul(etaf, g0sum.im), tim = ff_neg(ff_mul(etaf, g0sum.re));
+        S.dff[mm] = make_float4(dsum.re.hi, dsum.re.lo, dsum.im.hi, dsum.im.lo);
+        S.tff[mm] = make_float4(tre.hi, tre.lo, tim.hi, tim.lo);
       }
       __syncthreads();
       // F: accumulate w P_l(s) x (theta-coefficients) for the node's panel, in

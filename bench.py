@@ -389,7 +389,7 @@ def run_ours(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 operator + f64 (assembly, Krylov, refinement)",
+        "vs_baseline": None, "dtype": "f32 inner operator; f64 + float-float (assembly, refinement residual, far field); f64 Krylov",
         "data": "synthetic (seeded quasi-axisymmetric bodies)",
         "config": {"workload": sc.name, "n_bodies": len(sc.bodies), "N": N, "R": R, "k": sc.k, "eta": sc.eta,
                    "tol": args.tol, "far_field_dirs": M, "parallelism": f"replicas x{world}",

@@ -247,3 +247,33 @@ def test_hundred_bodies_sixteen_rhs_residual_rows():
         row = self_block_rows_parallel(nodes[bi], [gidx - off[bi]], sc.k, sc.eta, workers=1)[0]
         Am[i] += row @ m[off[bi]:off[bi + 1]]
     assert np.max(np.abs(Am - bb[rows])) < 1e-9 * np.max(np.abs(bb))
+
+
+def test_thousand_bodies_four_rhs_residual_rows():
+    """1000 bodies x 512 nodes, k = 3, 4 incident directions (N = 512,000): the
+    mixed solve of all 4 columns, then sampled rows of b - A mu from oracle
+    self-block rows and explicit pair sums over all 511,488 other-body nodes."""
+    import torch
+    import paper_2606_31380_b300 as q
+    from oracle.selfblock import self_block_rows_parallel
+    sc = scenes.config(3)
+    ctx = make_ctx(sc)
+    ctx.assemble()
+    R = sc.n_rhs
+    b = torch.zeros((ctx.N, R), dtype=torch.complex128, device="cuda")
+    ctx.incident_plane(sc.directions, b)
+    mu = torch.zeros_like(b)
+    st = ctx.solve(b, mu, q.PREC_FP32, tol=1e-11)
+    assert st["rel_residual"] <= 1e-11
+    nodes = [body_nodes(x) for x in sc.bodies]
+    off = ctx.body_offsets()
+    m = mu.cpu().numpy()
+    bb = op.incident(nodes, sc.directions, sc.k)
+    w = np.concatenate([n.w for n in nodes])
+    rows = [0, 512 * 433 + 100, 512 * 999 + 511]
+    Am = op.pair_sum(nodes, w[:, None] * m, sc.k, sc.eta, targets=rows)
+    for i, gidx in enumerate(rows):
+        bi = int(np.searchsorted(off, gidx, side="right") - 1)
+        row = self_block_rows_parallel(nodes[bi], [gidx - off[bi]], sc.k, sc.eta, workers=1)[0]
+        Am[i] += row @ m[off[bi]:off[bi + 1]]
+    assert np.max(np.abs(Am - bb[rows])) < 1e-9 * np.max(np.abs(bb))

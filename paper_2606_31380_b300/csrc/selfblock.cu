@@ -65,7 +65,7 @@ struct alignas(16) RowShared {
   float2 fs[3][MAXM2];          // samples of cos(k rho), sinc(k rho), q3(k rho) (float-float)
   double fc[3][MAXN1 + 1];      // their cosine coefficients
   double pr[MAXN1 + 1], pz[MAXN1 + 1], f2[MAXN1 + 1];
-  double cA[MAXN + 2], cB[MAXN + 2], cC[MAXN + 3];  // the three phi-convolutions (see stage D)
+  double cA[MAXN + 2], cBr[MAXN + 2], cBz[MAXN + 2], cC[MAXN + 3];  // the phi-convolutions (stage D)
   float4 gff[3][MAXN + 2];  // G^, d_r G^, d_z G^ (phi coefficients, m <= N+1): re hi, re lo, im hi, im lo
   float4 eff[MAXN + 2];     // (cos hi, cos lo, sin hi, sin lo)(m alpha)
   double ecs[8 + (MAXN + 9) / 8], esn[8 + (MAXN + 9) / 8];  // cos/sin(j alpha), j < 8, then of 8 l alpha
@@ -82,7 +82,7 @@ struct alignas(16) RowShared {
   float4 csff[2 * MAXN];                // (cos hi, cos lo, sin hi, sin lo)(2 pi j / 2N)
   float2 plff[MAXORD];                  // outer weight x P_l
   float2 fcff[2][MAXN1 + 1];            // cos^ and sinc^ coefficients (convolution inputs)
-  float2 sg0ff[MAXP + 1], sdqff[MAXP + 1];  // g^ and Q' scale
+  float2 sg0ff[MAXP + 1], srff[MAXP + 1], szff[MAXP + 1];  // g^, dchi_r Q' scale, dchi_z Q' scale
 };
 
 struct AsmBody {
@@ -598,9 +598,12 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
         const double g0 = q[m] * scale, gd = dq[m] * scale;
         S.sg0[m] = g0;
         S.sdq[m] = gd;
-        const ff a = ff_from_double(g0), b = ff_from_double(gd);
+        // Q' scale grows like r / h^2 near the singular point (beyond FP32's range on
+        // refined panels); the products with dchi_r, dchi_z grow only like 1/(r h)
+        const ff a = ff_from_double(g0), b = ff_from_double(dchi_r * gd), cz = ff_from_double(dchi_z * gd);
         S.sg0ff[m] = make_float2(a.hi, a.lo);
-        S.sdqff[m] = make_float2(b.hi, b.lo);
+        S.srff[m] = make_float2(b.hi, b.lo);
+        S.szff[m] = make_float2(cz.hi, cz.lo);
       }
       if (!kz) {
         for (int e = tid; e <= M2; e += NT) {
@@ -650,23 +653,24 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
           S.pr[n] = k3 * ((dr + rt) * S.fc[2][n] - 0.5 * rt * (Qm + Qp));
           S.pz[n] = -k3 * c * S.fc[2][n];
         }
-        // D: the three convolutions the real parts need (all sequences even in n),
-        //   A_m = sum_n cos^_n g^_{m-n},  B_m = sum_n cos^_n (Q' scale)_{m-n},
+        // D: the four convolutions the real parts need (all sequences even in n),
+        //   A_m = sum_n cos^_n g^_{m-n},  B^r_m, B^z_m = sum_n cos^_n (dchi_{r,z} Q' scale)_{m-n},
         //   C_m = sum_n sinc^_n g^_{m-n}   (m = 0..N+1; C also at N+2),
-        // because d_r g^ and d_z g^ are combinations of g^ and Q' scale, and the
+        // because d_r g^ = dchi_r Q' scale - g^/(2r) and d_z g^ = dchi_z Q' scale, and the
         // sinc-weighted terms are C_m and its cos(phi)-shift (C_{m-1} + C_{m+1})/2.
         // (in float-float: these are sums of FP64-computed products, ~48 bits suffice)
         const int L0 = N + 2;
-        for (int e = tid; e < 3 * L0 + 1; e += NT) {
-          const float2* f = e < 2 * L0 ? S.fcff[0] : S.fcff[1];
-          const float2* g = (e >= L0 && e < 2 * L0) ? S.sdqff : S.sg0ff;
-          const int m = e < L0 ? e : (e < 2 * L0 ? e - L0 : e - 2 * L0);
+        for (int e = tid; e < 4 * L0 + 1; e += NT) {
+          const int part = min(e / L0, 3);  // 0 A, 1 B^r, 2 B^z, 3 C
+          const float2* f = part < 3 ? S.fcff[0] : S.fcff[1];
+          const float2* g = part == 1 ? S.srff : (part == 2 ? S.szff : S.sg0ff);
+          const int m = e - part * L0;
           ff sum = ff_mul(ff{f[0].x, f[0].y}, ff{g[m].x, g[m].y});
           for (int n = 1; n <= n1; ++n) {
             const float2 ga = g[abs(m - n)], gb = g[m + n];
             sum = ff_add(sum, ff_mul(ff{f[n].x, f[n].y}, ff_add(ff{ga.x, ga.y}, ff{gb.x, gb.y})));
           }
-          (e < L0 ? S.cA : (e < 2 * L0 ? S.cB : S.cC))[m] = ff_to_double(sum);
+          (part == 0 ? S.cA : (part == 1 ? S.cBr : (part == 2 ? S.cBz : S.cC)))[m] = ff_to_double(sum);
         }
         __syncthreads();
       }
@@ -689,10 +693,10 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
             im = m <= n1 ? S.f2[m] : 0.0;
           } else if (comp == 1) {
             const double cbar = 0.5 * (S.cC[m == 0 ? 1 : m - 1] + S.cC[m + 1]);
-            re = (dchi_r * S.cB[m] - S.cA[m] * inv2r - k2 * ((dr + rt) * S.cC[m] - rt * cbar)) * INV_2PI;
+            re = (S.cBr[m] - S.cA[m] * inv2r - k2 * ((dr + rt) * S.cC[m] - rt * cbar)) * INV_2PI;
             im = m <= n1 ? S.pr[m] : 0.0;
           } else {
-            re = (dchi_z * S.cB[m] + k2 * c * S.cC[m]) * INV_2PI;
+            re = (S.cBz[m] + k2 * c * S.cC[m]) * INV_2PI;
             im = m <= n1 ? S.pz[m] : 0.0;
           }
           const ff a = ff_from_double(re), b = ff_from_double(im);

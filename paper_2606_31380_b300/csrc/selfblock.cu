@@ -930,7 +930,13 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   if ((rc = qams_dev_alloc(c, &d_counts, 2 * sizeof(unsigned long long)))) return rc;
   QAMS_CUDA(cudaMemsetAsync(d_counts.p, 0, 2 * sizeof(unsigned long long), st));
   const size_t smem = qams_selfblock_smem(max_nb, pstride);
-  QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // The attribute is process-wide: requests served concurrently must not lower it under
+  // one another, so it is always set to the kernel's largest possible launch size.
+  static_assert(sizeof(RowShared) + 2 * sizeof(double) * BATCH * (MAXP + 2) +
+                        2 * sizeof(float4) * MAXORD * 2 * MAXN <= 227 * 1024,
+                "largest self-block launch exceeds the shared memory of a CTA");
+  const int smem_max = (int)qams_selfblock_smem(MAXORD * 2 * MAXN, MAXP + 2);
+  QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   const long long chunk = 1 << 20;
   for (long long r0 = 0; r0 < c->N; r0 += chunk) {

@@ -24,9 +24,9 @@
 //
 // The outer s-integral replaces the paper's generalised Gaussian tables (not
 // available) with a composite rule: dyadic sub-panels toward the
-// (near-)singular point with 2 order + 4 Gauss-Legendre nodes on the
-// outermost (where P_l varies fastest next to the panel end), order + 4 on
-// the next and 12 on the inner ones, and a graded innermost panel (u^6
+// (near-)singular point with max(2 order + 4, 36) Gauss-Legendre nodes on the
+// outermost (where P_l varies fastest next to the panel end), max(order + 4, 20)
+// on the next and 12 on the inner ones, and a graded innermost panel (u^6
 // substitution, 20 nodes) for the logarithm.  Ring-target geometry uses
 // difference formulas in h = s - s_t so that r - r~ and c keep full relative
 // precision as h -> 0 (the double-layer pieces each grow like 1/|h| and cancel).
@@ -361,6 +361,12 @@ __device__ __forceinline__ ffc ephase(float4 cs, bool nonneg) {
   return {c, nonneg ? ff_neg(sn) : sn};
 }
 
+// Nodes of the two outermost dyadic levels of a piece: they carry the Lagrange
+// factor P_l across half (and a quarter) of the piece, so they grow with the order,
+// with a floor for long low-order panels where the kernel itself varies on that scale.
+__host__ __device__ __forceinline__ int level0_nodes(int order) { return 2 * order + 4 > 36 ? 2 * order + 4 : 36; }
+__host__ __device__ __forceinline__ int level1_nodes(int order) { return order + 4 > 20 ? order + 4 : 20; }
+
 // Rule tables of one order (see qams_assemble_launch for the layout).
 struct Rules {
   const double *d0_x, *d0_w, *dy_x, *dy_w, *g12_x, *g12_w, *in_x, *in_w, *ad_x, *ad_w;
@@ -377,10 +383,10 @@ __device__ void outer_node(const RowShared& S, const Rules& R, int order, int id
   int j = idx - (pc > 0 ? S.pc_end[pc - 1] : 0);
   const double h0 = S.pc_h0[pc], L = S.pc_L[pc], aL = fabs(L);
   const int K = S.pc_K[pc];
-  const int ng = order + 4;
+  const int n0 = level0_nodes(order), n1l = level1_nodes(order);
   double top = 1.0;
   for (int kk = 0; kk < K; ++kk) {
-    const int nk = kk == 0 ? ng + order : (kk == 1 ? ng : 12);
+    const int nk = kk == 0 ? n0 : (kk == 1 ? n1l : 12);
     const double bot = 0.5 * top;
     if (j < nk) {
       const double* kx = kk == 0 ? R.d0_x : (kk == 1 ? R.dy_x : R.g12_x);
@@ -435,11 +441,11 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   const int lt = (t % per_panel) / nth;
   const int jt = t % nth;
   const double* gl_x = rules + B.rule;              // [order] on [-1,1]
-  const double* dy_x = gl_x + 2 * order;            // [order+4] on [0,1]
-  const double* dy_w = dy_x + (order + 4);
-  const double* d0_x = dy_w + (order + 4);          // [2 order+4] on [0,1], outermost level
-  const double* d0_w = d0_x + (2 * order + 4);
-  const double* in_x = d0_w + (2 * order + 4);      // [20]
+  const double* dy_x = gl_x + 2 * order;            // [level1_nodes] on [0,1]
+  const double* dy_w = dy_x + level1_nodes(order);
+  const double* d0_x = dy_w + level1_nodes(order);  // [level0_nodes] on [0,1], outermost level
+  const double* d0_w = d0_x + level0_nodes(order);
+  const double* in_x = d0_w + level0_nodes(order);  // [20]
   const double* in_w = in_x + 20;
   const double* ad_x = in_w + 20;                   // [16]
   const double* ad_w = ad_x + 16;
@@ -486,7 +492,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
         if (i == p) K = max(5, (int)ceil(log2(aL / (0.5 * dpole))));
         else K = max(6, (int)ceil(log2(aL / (3.2 * fabs(h0)))));
         K = min(K, 14);
-        nq += (2 * order + 4) + (order + 4) + 12 * (K - 2) + (i == p ? 20 : 16);
+        nq += level0_nodes(order) + level1_nodes(order) + 12 * (K - 2) + (i == p ? 20 : 16);
         S.pc_h0[npc] = h0;
         S.pc_L[npc] = L;
         S.pc_K[npc] = K;
@@ -855,12 +861,12 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
       qams_gauss_legendre(d.order, x, w);
       rules.insert(rules.end(), x.begin(), x.end());
       rules.insert(rules.end(), w.begin(), w.end());
-      qams_gauss_legendre(d.order + 4, x, w);
+      qams_gauss_legendre(level1_nodes(d.order), x, w);
       for (auto& v : x) v = 0.5 * (v + 1.0);
       for (auto& v : w) v *= 0.5;
       rules.insert(rules.end(), x.begin(), x.end());
       rules.insert(rules.end(), w.begin(), w.end());
-      qams_gauss_legendre(2 * d.order + 4, x, w);
+      qams_gauss_legendre(level0_nodes(d.order), x, w);
       for (auto& v : x) v = 0.5 * (v + 1.0);
       for (auto& v : w) v *= 0.5;
       rules.insert(rules.end(), x.begin(), x.end());

@@ -49,7 +49,7 @@ def test_sphere_block_matches_oracle_and_eigenvalues():
 
 
 @pytest.mark.parametrize("k,eta,disc", [(5.0, 1.0, (2, 16, 32)), (15.0, 1.0, (2, 12, 24)), (3.0, 0.0, (1, 16, 32)),
-                                        (1e-9, 0.0, (2, 8, 16))])
+                                        (1e-9, 0.0, (2, 8, 16)), (3.0, 1.0, (1, 8, 16))])
 def test_curved_body_rows_match_oracle(k, eta, disc):
     body = scenes.Body(*disc, **CURVED, rotation=scenes.rot_zy(0.7, 2.1), center=(1.0, -2.0, 0.5))
     sc = scenes.Scene("curved", [body], k, eta, scenes.paper_direction())

@@ -328,7 +328,10 @@ def run_ours(args, rank, world, local_rank):
     asm_alone = e0.elapsed_time(e1) / 1e3
     asm_counts = ctx.assembly_counts()
     flops = assembly_flops(sc, asm_counts)
-    peak64 = 1.25
+    # FP64 peak from the unit counts: 2 FP64 lanes per clock per SM (the issue rate ncu
+    # reports for DFMA) x 2 FLOP x SMs x the maximum SM clock
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    peak64 = 2 * 2 * sms * 2.032e9 / 1e12
     # cuBLAS DGEMM rate on this GPU (1.05 TFLOP/s when last measured); off by default so
     # that the run's launch list holds only the library's own kernels
     peak64_meas = fp64_peak_tflops(torch) if args.measure_fp64_peak else 1.05
@@ -407,9 +410,10 @@ def run_ours(args, rank, world, local_rank):
         "assembly_outer_nodes": {"modal": asm_counts[0], "far": asm_counts[1]},
         "roofline": {"kernel": "selfblock_kernel (FP64 self-block assembly)", "bound": "alu",
                      "achieved": achieved, "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64,
-                     "traffic": None, "peak_note": "nominal dense FP64 1.25 TFLOP/s; cuBLAS DGEMM "
-                     "%.3f TFLOP/s on this GPU%s" % (peak64_meas, "" if args.measure_fp64_peak else
-                                                     " (earlier measurement)")},
+                     "traffic": None,
+                     "peak_note": ("derived: 2 FP64 lanes/clk/SM x 2 FLOP x %d SMs x 2.032 GHz (nominal 1.25); "
+                                   "cuBLAS DGEMM %.3f TFLOP/s on this GPU%s"
+                                   % (sms, peak64_meas, "" if args.measure_fp64_peak else " (earlier measurement)"))},
         "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,

@@ -3,7 +3,9 @@
 //   F^D_j = int [(|J| n_r) K^r + (|J| n_z) K^z] L_j dtheta,  F^S_j = -i eta int G L_j dtheta,
 // for every panel i within one of the target's panel (Eq. sx); farther panels
 // take the plain smooth rule.  The double layer integrates the exact
-// area-weighted normal |J| n_r = r l'(1 - kappa r cos theta), |J| n_z = -r r'
+// area-weighted normal |J| n_r = a0 + a1 cos theta, |J| n_z = b0 + b1 cos theta
+// + b2 sin theta (arc-axis bodies: r l'(1 - kappa r cos theta) and -r r'; the
+// paper's horizontal-ring shapes: r z' and -r (r' + x_c' cos + y_c' sin))
 // against an interpolant of mu; the single layer keeps the interpolant of
 // mu |J| (the paper's); on bodies of revolution the two coincide.
 //

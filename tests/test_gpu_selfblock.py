@@ -123,3 +123,28 @@ def test_apply_full_size_sampled_rows():
     ctx.apply(xd, y, q.PREC_FF)
     torch.cuda.synchronize()
     assert rel_err(y.cpu().numpy()[rows], ref) < 1e-12
+
+
+def test_limits_and_single_body():
+    """A body beyond the kernel's limits (n_theta/2 > 32) is refused at assembly
+    with QAMS_EINVAL; a single body has no inter-body part: its pair sum is zero
+    and the operator apply equals its self-block product exactly."""
+    import torch
+    import paper_2606_31380_b300 as q
+    big = scenes.Body(1, 8, 80, 0.5, (0.1,), (), 1.0, 0.2)
+    ctx = make_ctx(scenes.Scene("big", [big], 2.0, 1.0, scenes.paper_direction()))
+    with pytest.raises(q.QamsError) as err:
+        ctx.assemble()
+    assert err.value.code == -1
+    one = scenes.Body(1, 8, 16, 0.5, (0.1,), (), 1.0, 0.2)
+    ctx = make_ctx(scenes.Scene("one", [one], 2.0, 1.0, scenes.paper_direction()))
+    ctx.assemble()
+    x = torch.from_numpy(scenes.rhs_seeded(ctx.N, 2, 3)).cuda()
+    y = torch.full_like(x, float("nan"))
+    ctx.pairsum(x, y, q.PREC_FP64)
+    assert float(torch.abs(y).max()) == 0.0
+    ya, yb = torch.empty_like(x), torch.empty_like(x)
+    ctx.apply(x, ya, q.PREC_FP64)
+    ctx.selfblock_apply(x, yb, q.PREC_FP64)
+    torch.cuda.synchronize()
+    assert torch.equal(ya, yb)

@@ -187,7 +187,8 @@ int qams_copy_preconditioner(const qams_ctx* ctx, int body, void* dst_dev, void*
 /* Operator apply (Eq. linearsys): y = (1/2 I + D - i eta S) x for [N][R]
  * complex x (densities mu, weights not folded in), self blocks times x
  * plus the inter-body pair sum of w x.  QAMS_PREC_FP64 works in complex128,
- * QAMS_PREC_FP32 in complex64 with the complex64 block copy.  Requires
+ * QAMS_PREC_FP32 in complex64 with the complex64 block copy, QAMS_PREC_FF in
+ * complex128 with the float-float pair sum and the complex128 blocks.  Requires
  * qams_assemble.  Uses a library-owned workspace of N*R complex. */
 int qams_apply(qams_ctx* ctx, int R, const void* x_dev, void* y_dev, int precision, void* stream);
 
@@ -207,14 +208,15 @@ int qams_precond_apply(qams_ctx* ctx, int R, const void* x_dev, void* y_dev, int
  * GMRES with the FP64 apply, stop at ||b - A mu|| <= tol ||b|| per column.
  * precision = QAMS_PREC_FP32: iterative refinement -- each correction solves
  * A d = r by GMRES with the FP32 apply to a relative reduction inner_tol,
- * then mu += d and r = b - A mu with the FP64 apply, until r meets tol.  The
+ * then mu += d and r = b - A mu with the apply of `residual` (float-float by
+ * default, FP64-accurate), until r meets tol.  The
  * Krylov basis and Gram-Schmidt (classical, applied twice) are FP64 in both
  * modes.  With precondition = 1 GMRES runs on A P^{-1} with the block-
  * Jacobi preconditioner of qams_build_preconditioner (built by the first
  * solve that asks for it) and returns mu = P^{-1} z.  A cancelled server
  * request stops between restart cycles with QAMS_ECANCELLED.
  * qams_solve_opts_default fills: FP32, restart 50, max_iters 1000,
- * tol 1e-11, inner_tol 1e-5, max_refine 12, precondition 1. */
+ * tol 1e-11, inner_tol 1e-5, max_refine 12, precondition 1, residual FF. */
 typedef struct {
   int precision;
   int restart;      /* m, 1..200 */
@@ -229,11 +231,11 @@ typedef struct {
 
 typedef struct {
   int iterations;      /* Arnoldi steps (all corrections)          */
-  int refinements;     /* FP64 residual evaluations (FP32 mode)    */
+  int refinements;     /* residual evaluations (FP32 mode)         */
   double rel_residual; /* max over columns of ||b - A mu|| / ||b|| */
   double solve_ms;     /* device time of the call (CUDA events)    */
   int applies_fp32;    /* operator applies with the FP32 path      */
-  int applies_fp64;    /* operator applies with the FP64 path      */
+  int applies_fp64;    /* FP64-accurate applies (FP64 or FF)       */
 } qams_solve_stats;
 
 void qams_solve_opts_default(qams_solve_opts* opts);

@@ -393,7 +393,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64",
-        "precision_note": "f32 inner operator; f64 and float-float (pairs of f32) in the assembly, refinement residual and far field; f64 Krylov basis",
+        "precision_note": ("f32 inner operator; f64 and float-float (pairs of f32) in the assembly, "
+                           "refinement residual and far field; f64 Krylov basis"),
         "data": "synthetic (seeded quasi-axisymmetric bodies)",
         "config": {"workload": sc.name, "n_bodies": len(sc.bodies), "N": N, "R": R, "k": sc.k, "eta": sc.eta,
                    "tol": args.tol, "far_field_dirs": M, "parallelism": f"replicas x{world}",

@@ -131,6 +131,13 @@ int qams_body_offsets(const qams_ctx* ctx, long long* offsets_host);
  * Any pointer may be NULL.  Blocking. */
 int qams_get_nodes(const qams_ctx* ctx, double* x_host, double* n_host, double* w_host);
 
+/* The Nystrom nodes of one body (Eq. para_quasi, Sec. 3.1, Eq. sx) without a
+ * context or device: x_host, n_host [n][3] world positions and unit normals,
+ * w_host [n] weights |J| (2 pi / n_theta) omega, n = n_panels order n_theta,
+ * in the node order of qams_get_nodes.  Host only; any output may be NULL.
+ * Errors: QAMS_EINVAL (the descriptor conditions of qams_set_bodies). */
+int qams_body_nodes(const qams_body_desc* body, double* x_host, double* n_host, double* w_host);
+
 /* Wavenumber k > 0 and combined-layer coupling eta (0 = pure double layer,
  * Eq. multi-double; 1 = the default of the Sec. 2 Remark). */
 int qams_set_wavenumber(qams_ctx* ctx, double k, double eta);

@@ -5,8 +5,8 @@ CUDA for sm_103a, declared in ``include/qams.h``).  This package is only its
 ctypes binding; there is no CPU fallback: importing it without the built
 library, or calling it without a CUDA device, raises.
 """
-from ._binding import (PREC_FF, PREC_FP32, PREC_FP64, Context, QamsError, Server, body_desc_array, footprint,  # noqa: F401
-                       kernel_launches, lib_path, load_library)
+from ._binding import (PREC_FF, PREC_FP32, PREC_FP64, Context, QamsError, Server,  # noqa: F401
+                       body_desc_array, body_nodes, footprint, kernel_launches, lib_path, load_library)
 
 __all__ = ["Context", "Server", "QamsError", "PREC_FP64", "PREC_FP32", "PREC_FF", "load_library", "lib_path",
-           "body_desc_array", "footprint", "kernel_launches"]
+           "body_desc_array", "body_nodes", "footprint", "kernel_launches"]

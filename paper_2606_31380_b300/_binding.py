@@ -94,6 +94,7 @@ def load_library():
         "qams_solve": (i, [vp, i, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveStats), vp]),
         "qams_farfield": (i, [vp, i, vp, i, vp, vp, vp]),
         "qams_field": (i, [vp, i, vp, i, vp, vp, vp]),
+        "qams_body_nodes": (i, [vp, vp, vp, vp]),
         "qams_selfblock_apply": (i, [vp, i, vp, vp, i, vp]),
         "qams_precond_apply": (i, [vp, i, vp, vp, i, vp]),
     }
@@ -350,6 +351,18 @@ class Context:
 
 
 QAMS_EAGAIN = -10
+
+
+def body_nodes(body):
+    """Host-side Nystrom nodes of one body: world positions (n, 3), unit normals
+    (n, 3), weights (n,) -- no device needed."""
+    lib = load_library()
+    arr, keep = body_desc_array([body])
+    n = body.n_panels * body.order * body.n_theta
+    x, nn, w = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+    _check(lib.qams_body_nodes(C.cast(arr, C.c_void_p), x.ctypes.data_as(C.c_void_p),
+                               nn.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)), "qams_body_nodes")
+    return x, nn, w
 
 
 def footprint(bodies, R: int, restart: int = 50) -> int:

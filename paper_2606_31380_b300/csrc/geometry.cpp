@@ -206,6 +206,39 @@ qams_body_desc qams_desc_view(const BodyCopy& bc) {
   return d;
 }
 
+// Nodes of one body (order panel -> Gauss-Legendre node -> azimuth): world
+// position, world normal, weight w = |J| (2 pi / n_theta) omega and |J|.
+static void body_nodes_into(const BodyCopy& bc, double* x, double* n, double* w, double* jac_out) {
+  const qams_body_desc& d = bc.d;
+  Shape sh{bc};
+  std::vector<double> gx, gw;
+  qams_gauss_legendre(d.order, gx, gw);
+  long long idx = 0;
+  const double dth = 2.0 * M_PI / d.n_theta;
+  for (int i = 0; i < d.n_panels; ++i) {
+    const double lo = bc.breaks[i], hi = bc.breaks[i + 1];
+    for (int l = 0; l < d.order; ++l) {
+      const double s = 0.5 * (lo + hi) + 0.5 * (hi - lo) * gx[l];
+      const double om = 0.5 * (hi - lo) * gw[l];
+      for (int j = 0; j < d.n_theta; ++j, ++idx) {
+        double p[3], nl[3], jac;
+        sh.eval(s, j * dth, p, nl, &jac);
+        for (int r = 0; r < 3; ++r) {
+          double xr = d.center[r], nr = 0.0;
+          for (int q = 0; q < 3; ++q) {
+            xr += d.rotation[3 * r + q] * p[q];
+            nr += d.rotation[3 * r + q] * nl[q];
+          }
+          if (x) x[3 * idx + r] = xr;
+          if (n) n[3 * idx + r] = nr;
+        }
+        if (w) w[idx] = jac * dth * om;
+        if (jac_out) jac_out[idx] = jac;
+      }
+    }
+  }
+}
+
 int qams_build_nodes(qams_ctx* c) {
   long long N = 0;
   for (auto& bh : c->bodies) {
@@ -218,36 +251,17 @@ int qams_build_nodes(qams_ctx* c) {
   c->hn.assign(3 * N, 0.0);
   c->hw.assign(N, 0.0);
   c->hj.assign(N, 0.0);
-  for (auto& bh : c->bodies) {
-    const qams_body_desc& d = bh.d;
-    Shape sh{bh};
-    std::vector<double> gx, gw;
-    qams_gauss_legendre(d.order, gx, gw);
-    long long idx = bh.offset;
-    double dth = 2.0 * M_PI / d.n_theta;
-    for (int i = 0; i < d.n_panels; ++i) {
-      double lo = bh.breaks[i];
-      double hi = bh.breaks[i + 1];
-      for (int l = 0; l < d.order; ++l) {
-        double s = 0.5 * (lo + hi) + 0.5 * (hi - lo) * gx[l];
-        double om = 0.5 * (hi - lo) * gw[l];
-        for (int j = 0; j < d.n_theta; ++j, ++idx) {
-          double p[3], nl[3], jac;
-          sh.eval(s, j * dth, p, nl, &jac);
-          for (int r = 0; r < 3; ++r) {
-            double xr = d.center[r], nr = 0.0;
-            for (int q = 0; q < 3; ++q) {
-              xr += d.rotation[3 * r + q] * p[q];
-              nr += d.rotation[3 * r + q] * nl[q];
-            }
-            c->hx[3 * idx + r] = xr;
-            c->hn[3 * idx + r] = nr;
-          }
-          c->hw[idx] = jac * dth * om;
-          c->hj[idx] = jac;
-        }
-      }
-    }
-  }
+  for (auto& bh : c->bodies)
+    body_nodes_into(bh, c->hx.data() + 3 * bh.offset, c->hn.data() + 3 * bh.offset, c->hw.data() + bh.offset,
+                    c->hj.data() + bh.offset);
+  return QAMS_OK;
+}
+
+extern "C" int qams_body_nodes(const qams_body_desc* desc, double* x_host, double* n_host, double* w_host) {
+  if (!desc) return QAMS_EINVAL;
+  BodyCopy bc;
+  const int rc = qams_copy_body(*desc, &bc);
+  if (rc) return rc;
+  body_nodes_into(bc, x_host, n_host, w_host, nullptr);
   return QAMS_OK;
 }

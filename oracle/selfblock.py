@@ -33,7 +33,11 @@ vector-valued Gauss-Kronrod 7/15 pair until the estimated error is below
 
 Pins: tests/test_oracle_selfblock.py (Gauss identity at k = 0, sphere
 eigenvalues of S and D, Mie series, interior point sources, circulant
-structure on bodies of revolution).
+structure on bodies of revolution) and
+tests/test_oracle_selfblock_bruteforce.py (single entries on the self and
+adjacent panels of a curved arc-axis body and of the paper's conch at
+k = 3 and 10 against an independent adaptive 2-D cubature of the defining
+integral, in extended precision, to 1e-12 of the row maximum).
 """
 from __future__ import annotations
 

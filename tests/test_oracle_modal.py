@@ -41,10 +41,15 @@ def test_near_ring_against_adaptive_quadrature(k):
         g = lambda p: mpmath.exp(1j * k * rho(p)) / (4 * mpmath.pi * rho(p)) * mpmath.cos(m * p)
         gr = lambda p: (mpmath.exp(1j * k * rho(p)) * (1j * k * rho(p) - 1) / (4 * mpmath.pi * rho(p) ** 3)
                         * (R - RT * mpmath.cos(p)) * mpmath.cos(m * p))
+        # the source derivative along the ring axis, d/dz_y G with c = z_t - z
+        gz = lambda p: (-mpmath.exp(1j * k * rho(p)) * (1j * k * rho(p) - 1) / (4 * mpmath.pi * rho(p) ** 3)
+                        * C * mpmath.cos(m * p))
         ref_g = complex(2 * mpmath.quad(g, brk))
         ref_r = complex(2 * mpmath.quad(gr, brk))
+        ref_z = complex(2 * mpmath.quad(gz, brk))
         assert abs(G[m] - ref_g) < 1e-13 * abs(ref_g)
         assert abs(Gr[m] - ref_r) < 1e-13 * abs(ref_r)
+        assert abs(Gz[m] - ref_z) < 1e-13 * abs(ref_z)
 
 
 def test_k_to_zero_limit():

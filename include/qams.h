@@ -270,19 +270,23 @@ int qams_solve(qams_ctx* ctx, int R, const void* rhs_dev, void* mu_dev, const qa
  *                     [n_bodies] = N, strictly increasing (host memory);
  *   centers_host      [n_bodies][3]: body centres c_b (FP64, host memory);
  *   x32_dev           float4 [N]: node position minus its body's centre
- *                     (x, y, z) and quadrature weight w in .w;
- *   n32_dev           float4 [N]: unit normal (x, y, z), .w unused;
- *   sigma_dev, y_dev  complex64 [N][R], y overwritten (as in qams_pairsum).
+ *                     (x, y, z); .w is not read;
+ *   n32_dev           float4 [N]: unit normal (x, y, z), .w not read;
+ *   sigma_dev, y_dev  complex64 [N][R], y overwritten (as in qams_pairsum):
+ *                     sigma must already hold w mu, the quadrature weights
+ *                     folded in (Eq. multi2part).
  * Works on the current CUDA device.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls on a device share the one array:
- * calls that overlap on the GPU race (serialise them on one stream).
- * Nothing in the array needs to start at zero.  Blocking (returns after its
- * work on `stream` finished).
+ * the array's device address (cudaGetSymbolAddress) and keeps it for the
+ * life of the process; make that first call before any stream capture, and
+ * do not use this call again after a cudaDeviceReset in the same process.
+ * All calls on a device share the one array: calls that overlap on the GPU
+ * race (serialise them on one stream).  Nothing in the array needs to start
+ * at zero.  Blocking (returns after its work on `stream` finished).
  * When the per-split partial sums would not fit in the array, fewer source
  * splits are used (down to one, which needs no partial sums).
- * Errors: QAMS_EINVAL, QAMS_ESCRATCH (more than 4096 bodies or more than
- * 65536 target tiles of 128 nodes), QAMS_ECUDA. */
+ * Errors: QAMS_EINVAL (bad arguments, or `stream` in stream-capture mode:
+ * nothing is enqueued then), QAMS_ESCRATCH (more than 4096 bodies or more
+ * than 65536 target tiles of 128 nodes), QAMS_ECUDA. */
 int qams_pairsum_f32_static(int n_bodies, const long long* body_offsets_host, const double* centers_host,
                             const void* x32_dev, const void* n32_dev, int R, const void* sigma_dev, void* y_dev,
                             double k, double eta, void* stream);

@@ -499,7 +499,9 @@ constexpr int STATIC_MAX_DEVICES = 64;
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
 
 // Device address of g_static_scratch per device (host code cannot use the
-// symbol's name as a device pointer); filled on the first call on a device.
+// symbol's name as a device pointer); looked up once, on the first call on a
+// device.  A cudaDeviceReset ends the context the address belongs to, so
+// this entry point must not be used again in a process that reset the device.
 static void* g_static_ptr[STATIC_MAX_DEVICES];
 
 }  // namespace
@@ -515,6 +517,12 @@ extern "C" int qams_pairsum_f32_static(int n_bodies, const long long* body_offse
   if (body_offsets_host[0] != 0 || N < 1) return QAMS_EINVAL;
   for (int b = 0; b < n_bodies; ++b)
     if (body_offsets_host[b + 1] <= body_offsets_host[b]) return QAMS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the call waits for its own copies before returning; on a stream that is
+  // being captured that wait would invalidate the caller's capture
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  QAMS_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return QAMS_EINVAL;
   int dev = 0;
   QAMS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= STATIC_MAX_DEVICES) return QAMS_ESCRATCH;
@@ -524,7 +532,6 @@ extern "C" int qams_pairsum_f32_static(int n_bodies, const long long* body_offse
     g_static_ptr[dev] = p;
   }
   unsigned char* base = (unsigned char*)g_static_ptr[dev];
-  cudaStream_t st = (cudaStream_t)stream;
 
   // launch tables, built like qams_pairsum_prepare's (host memory only)
   std::vector<TargetTile> tiles;

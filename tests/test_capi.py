@@ -60,3 +60,21 @@ def test_descriptor_validation_on_host():
     for b in bad:
         with pytest.raises(q.QamsError):
             q.footprint([b], 1)
+
+
+def test_static_pairsum_rejects_oversized_input_before_any_device_work():
+    """qams_pairsum_f32_static refuses more bodies than its static scratch
+    holds (QAMS_ESCRATCH) before touching the device: no launch, no CUDA call."""
+    import ctypes as C
+    import numpy as np
+    import paper_2606_31380_b300 as q
+    lib = q.load_library()
+    nb = 4097
+    offs = np.arange(nb + 1, dtype=np.int64) * 4
+    cens = np.zeros((nb, 3), np.float64)
+    dummy = C.c_void_p(16)  # never dereferenced: the size check comes first
+    before = q.kernel_launches()
+    code = lib.qams_pairsum_f32_static(nb, offs.ctypes.data_as(C.c_void_p), cens.ctypes.data_as(C.c_void_p),
+                                       dummy, dummy, 1, dummy, dummy, 2.0, 1.0, None)
+    assert code == -9  # QAMS_ESCRATCH
+    assert q.kernel_launches() == before

@@ -19,12 +19,11 @@ pytestmark = pytest.mark.gpu
 FP32_TOL = 3e-5  # the FP32 pair-sum tolerance of the other GPU tests
 
 
-def test_static_scratch_pairsum_matches_allocating_entry_point():
+def _run(sc, Rs):
     import torch
 
     import paper_2606_31380_b300 as q
 
-    sc = scenes.small_scene(6, 1, 8, 20, k=4.0, eta=1.0, seed=13, box=9.0)  # 160-node bodies: ragged tiles
     ctx = q.Context(0)
     ctx.set_bodies(sc.bodies)
     ctx.set_wavenumber(sc.k, sc.eta)
@@ -43,7 +42,7 @@ def test_static_scratch_pairsum_matches_allocating_entry_point():
     offs = np.ascontiguousarray(off, np.int64)
     cens = np.ascontiguousarray(cen, np.float64)
     stream = torch.cuda.current_stream().cuda_stream
-    for call, R in enumerate([3, 1]):
+    for call, R in enumerate(Rs):
         sigma = torch.from_numpy(scenes.rhs_seeded(ctx.N, R, 20 + call)).to(torch.complex64).cuda()
         ref = torch.empty_like(sigma)
         ctx.pairsum(sigma, ref, q.PREC_FP32)
@@ -57,3 +56,17 @@ def test_static_scratch_pairsum_matches_allocating_entry_point():
         a, b = out.cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(a))
         assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < FP32_TOL
+    ctx.close()
+
+
+def test_static_scratch_pairsum_matches_allocating_entry_point():
+    """Six 160-node bodies (ragged target tiles), R = 3 then R = 1: several
+    source splits whose partial sums sit in the static scratch."""
+    _run(scenes.small_scene(6, 1, 8, 20, k=4.0, eta=1.0, seed=13, box=9.0), [3, 1])
+
+
+def test_static_scratch_pairsum_single_split_at_full_size():
+    """1000 bodies x 512 nodes at R = 16: the per-split partial sums (8 N R
+    bytes per split) no longer fit the 32 MiB scratch, so the call falls back
+    to one source split that writes y directly; then R = 4."""
+    _run(scenes.config(3), [16, 4])

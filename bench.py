@@ -2,14 +2,20 @@
 """Benchmark of the multi-body Nystrom solve on B300.
 
 One step = one full mixed-precision solve of a seeded scene: self-block
-assembly for the wavenumber, incident right-hand sides, GMRES with the FP32
-operator inside FP64 iterative refinement to ||b - A mu|| <= 1e-10 ||b|| (the
-metric asks for 1e-8 relative error; the error against the FP64 solve is
-reported), and
-the far field on 200 x 200 directions.  Geometry (qams_set_bodies) is
-resident before the timed region; the e2e figure repeats the step through
-the C ABI starting from host descriptors and ending with the densities and
-far field copied back to host memory.
+assembly for the wavenumber, incident right-hand sides, the block-Jacobi
+preconditioner, GMRES with the FP32 operator inside FP64 iterative
+refinement to ||b - A mu|| <= 1e-10 ||b|| (the metric asks for 1e-8
+relative error), and the far field on 200 x 200 directions.  The default
+workload is the largest configuration of the metric: 1000 bodies x 512
+nodes (N = 512,000), k = 3, 4 incident directions.  The 16- and 100-body
+workloads are measured in the same run (a few solves each) and reported
+under "other_workloads".  Per result the accuracy is given as the
+FP64-accurate residual of the returned densities and their distance to a
+solve refined to 1e-13 (and, where it is affordable, to the plain FP64
+GPU solve).  Geometry (qams_set_bodies) is resident before the timed
+region; the e2e figure repeats the step through the C ABI starting from
+host descriptors and ending with the densities and far field copied back
+to host memory.
 
 value = Nystrom pair-interactions per second over the whole step: the
 pair-sum evaluations of every operator apply in the solve (N^2 - sum n_b^2
@@ -124,11 +130,6 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-# FP32 pair (R = 1): 34 FP32 operations + 4 MUFU (rsqrt, rcp, sin, cos) + 4 FMA per
-# right-hand side; FP64 pair: 44 FP64 operations + rsqrt (counted as 4) incl. the
-# table-driven e^{ik rho} (15) -- counted from the kernel sources.
-FP32_OPS_PER_PAIR = 34
-FP64_OPS_PER_PAIR = 48
 # float-float pair: ~640 FP32 operations (the e^{ik rho} evaluation ~195, the
 # accumulation 72 per right-hand side) -- counted from the kernel source
 FF_OPS_PER_PAIR = 640
@@ -144,52 +145,6 @@ def _time_ms(torch, fn, reps=5):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
-
-
-def kernel_rooflines(torch, q, ctx, sc, N, R, pairs, device):
-    """Pair sums (ALU: FP32 pipe + MUFU, FP64 pipe) and block products (HBM),
-    each timed alone with CUDA events on the current stream."""
-    props = torch.cuda.get_device_properties(device)
-    sms = props.multi_processor_count
-    f = 2.032e9  # maximum SM clock (the sampled clock sits there under this load)
-    hbm = measured_peaks()[0]["hbm_gbs"]
-    s32 = torch.randn((N, R), dtype=torch.complex64, device="cuda")
-    y32 = torch.empty_like(s32)
-    s64 = s32.to(torch.complex128)
-    y64 = torch.empty_like(s64)
-    t32 = _time_ms(torch, lambda: ctx.pairsum(s32, y32, q.PREC_FP32))
-    t64 = _time_ms(torch, lambda: ctx.pairsum(s64, y64, q.PREC_FP64), reps=2)
-    yff = torch.empty_like(s64)
-    tff = _time_ms(torch, lambda: ctx.pairsum(s64, yff, q.PREC_FF), reps=3)
-    ff_diff = float(torch.linalg.norm(yff - y64) / torch.linalg.norm(y64))
-    peakff = 128 * sms * f / (FF_OPS_PER_PAIR + 72 * (R - 1))
-    # FP32: min over the FP32 pipe (128 lanes/SM/clk) and MUFU (16/SM/clk, 4 per pair)
-    peak32 = min(128 * sms * f / (FP32_OPS_PER_PAIR + 4 * R), 16 * sms * f / 4)
-    peak64 = 2 * sms * f / (FP64_OPS_PER_PAIR + 4 * (R - 1))  # FP64 pipe: 2 lanes/SM/clk
-    entries = sum(b.n_nodes ** 2 for b in sc.bodies)
-    tb32 = _time_ms(torch, lambda: ctx.selfblock_apply(s32, y32, q.PREC_FP32))
-    tb64 = _time_ms(torch, lambda: ctx.selfblock_apply(s64, y64, q.PREC_FP64))
-    reps16 = (R + 15) // 16
-    gb32 = entries * 8 * reps16 / (tb32 / 1e3) / 1e9
-    gb64 = entries * 16 * reps16 / (tb64 / 1e3) / 1e9
-    return {
-        "pairsum_f32_kernel": {"ms": t32, "pairs_per_s": pairs / (t32 / 1e3), "bound": "alu",
-                               "peak_pairs_per_s": peak32, "frac": pairs / (t32 / 1e3) / peak32},
-        "pairsum_f64_kernel": {"ms": t64, "pairs_per_s": pairs / (t64 / 1e3), "bound": "alu (FP64 pipe)",
-                               "peak_pairs_per_s": peak64, "frac": pairs / (t64 / 1e3) / peak64},
-        "pairsum_ff_kernel": {"ms": tff, "pairs_per_s": pairs / (tff / 1e3), "bound": "alu (FP32 pipe)",
-                              "peak_pairs_per_s": peakff, "frac": pairs / (tff / 1e3) / peakff,
-                              "rel_diff_vs_fp64_kernel": ff_diff},
-        "block_apply_kernel<float2>": {"ms": tb32, "achieved": gb32, "peak": hbm, "unit": "GB/s",
-                                       "bound": "hbm", "frac": gb32 / hbm},
-        # complex128 entries: 4 FP64 operations per entry and right-hand side put the
-        # FP64 pipe (2 lanes/SM/clk) below the HBM stream
-        "block_apply_kernel<double2>": {"ms": tb64, "achieved": entries * R / (tb64 / 1e3), "unit": "entries/s",
-                                        "bound": "alu (FP64 pipe)", "peak": 2 * sms * f / 4,
-                                        "frac": entries * R / (tb64 / 1e3) / (2 * sms * f / 4),
-                                        "hbm_gbs": gb64},
-        "note": "pair peaks from the op counts above at the maximum SM clock; HBM peak of measured",
-    }
 
 
 def assembly_flops(scene, counts):
@@ -239,120 +194,226 @@ def job_value(pair_evals_per_rank: float, world: int, elapsed_max: float) -> flo
     return pair_evals_per_rank * world / elapsed_max
 
 
-def run_ours(args, rank, world, local_rank):
-    import numpy as np
+def pair_roofline(sms: int, f_hz: float, R: int) -> float:
+    """Pair-interactions/s ceiling of the FP32 pair sum at R right-hand sides:
+    min over the FP32 pipe (128 lanes/clk/SM, 30 + 4R operations per pair) and
+    MUFU (16/clk/SM, 4 per pair: rsqrt, rcp, sin, cos)."""
+    return min(128 * sms * f_hz / (30 + 4 * R), 16 * sms * f_hz / 4)
+
+
+def pair_roofline_tc(sms: int, f_hz: float, R: int) -> float:
+    """Ceiling of the pair sum whose multiply-adds run on the tensor cores:
+    the FP32 pipe evaluates K (30 operations per pair) and MUFU its 4
+    transcendental steps; the tensor pipe has ample room for the 4R MACs."""
+    return min(128 * sms * f_hz / 30, 16 * sms * f_hz / 4)
+
+
+def solve_step(q, ctx, sc, b, mu, u, xh, tol, record=None):
+    """One full mixed-precision solve: assembly for k, right-hand sides, GMRES
+    with iterative refinement, far field."""
     import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    ctx.assemble()
+    ev[1].record()
+    ctx.incident_plane(sc.directions, b)
+    st = ctx.solve(b, mu, q.PREC_FP32, tol=tol)
+    ev[2].record()
+    ctx.farfield(mu, xh, u)
+    ev[3].record()
+    if record is not None:
+        record.append((ev, st))
+    return st
 
-    import paper_2606_31380_b300 as q
+
+def accuracy(q, torch, ctx, sc, b, mu, fp64_solve: bool):
+    """Per-result accuracy of the mixed solve: its FP64-accurate residual
+    (float-float apply) and its distance to a solve refined to 1e-13; on
+    small workloads also to the plain FP64 GPU solve."""
+    R = sc.n_rhs
+    y = torch.empty_like(mu)
+    ctx.apply(mu, y, q.PREC_FF)
+    res = torch.linalg.norm(b - y, dim=0) / torch.linalg.norm(b, dim=0)
+    ref = torch.zeros_like(mu)
+    ctx.solve(b, ref, q.PREC_FP32, tol=1e-13)
+    out = {"rel_residual_fp64_accurate": float(res.max()),
+           "rel_err_vs_1e-13_solve": float(torch.linalg.norm(mu - ref) / torch.linalg.norm(ref))}
+    if fp64_solve:
+        m64 = torch.zeros_like(mu)
+        ctx.solve(b, m64, q.PREC_FP64, tol=1e-12)
+        out["rel_err_vs_fp64_gpu"] = float(torch.linalg.norm(mu - m64) / torch.linalg.norm(m64))
+    return out
+
+
+def run_workload(q, torch, cfg, steps, warmup, tol, local_rank, dist=None, rank=0, profile=False, clocks=None):
+    """Warm-up, then exactly ``steps`` timed solves between barriers and device
+    synchronisation; returns the context and the per-step records."""
     import scenes
-
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    sc = scenes.config(args.config, request_id=rank)  # replicas: independent request per rank
-    if args.bodies:
-        # a smaller case of the same workload (profiling captures)
-        sc = scenes.Scene(sc.name + f" (first {args.bodies} bodies)", sc.bodies[:args.bodies], sc.k, sc.eta,
-                          sc.directions)
+    sc = scenes.config(cfg, request_id=rank)  # replicas: an independent request per rank
     R = sc.n_rhs
     xh = far_directions()
-    M = xh.shape[0]
     ctx = q.Context(local_rank)
     ctx.set_bodies(sc.bodies)
     ctx.set_wavenumber(sc.k, sc.eta)
     N = ctx.N
-    pairs = sc.pair_count()
     b = torch.zeros((N, R), dtype=torch.complex128, device="cuda")
     mu = torch.zeros_like(b)
-    u = torch.zeros((M, R), dtype=torch.complex128, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def step(record=None):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record()
-        ctx.assemble()
-        ev[1].record()
-        ctx.incident_plane(sc.directions, b)
-        st = ctx.solve(b, mu, q.PREC_FP32, tol=args.tol)
-        ev[2].record()
-        ctx.farfield(mu, xh, u)
-        ev[3].record()
-        if record is not None:
-            record.append((ev, st))
-        return st
-
-    for _ in range(args.warmup):
-        step()
+    u = torch.zeros((xh.shape[0], R), dtype=torch.complex128, device="cuda")
+    ctx.assemble()
+    tuning = ctx.autotune(R)  # launch shapes for this body set and R (outside the timed region)
+    for _ in range(warmup):
+        solve_step(q, ctx, sc, b, mu, u, xh, tol)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = ClockSampler(local_rank)
-    clocks.start()
+    if clocks:
+        clocks.start()
+    if profile:
+        ctx.profile(True)
     launches0 = q.kernel_launches()
     recs = []
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0.record()
-    for _ in range(args.steps):
-        step(recs)
+    for _ in range(steps):
+        solve_step(q, ctx, sc, b, mu, u, xh, tol, recs)
     t1.record()
     torch.cuda.synchronize()
     launches = q.kernel_launches() - launches0
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     elapsed = t0.elapsed_time(t1) / 1e3
     if dist:
         elapsed = max_over_ranks(elapsed, dist, "cuda")
         dist.barrier()
-    step_ms = [r[0][0].elapsed_time(r[0][3]) for r in recs]
-    asm_ms = [r[0][0].elapsed_time(r[0][1]) for r in recs]
-    solve_ms = [r[0][1].elapsed_time(r[0][2]) for r in recs]
-    ff_ms = [r[0][2].elapsed_time(r[0][3]) for r in recs]
+    prof = {}
+    if profile:
+        for name, slot in (("pairsum_f32_kernel", q.PROF_PAIRSUM_FP32), ("pairsum_tc_kernel", q.PROF_PAIRSUM_TC),
+                           ("tc_block_kernel", q.PROF_BLOCK_TC), ("pairsum_ff_kernel", q.PROF_PAIRSUM_FF),
+                           ("block_apply_kernel<float2>", q.PROF_BLOCK_FP32),
+                           ("block_apply_kernel<double2>", q.PROF_BLOCK_FP64),
+                           ("selfblock_kernel", q.PROF_ASSEMBLY)):
+            prof[name] = ctx.profile_read(slot)
+        ctx.profile(False)
     applies = [r[1]["applies_fp32"] + r[1]["applies_fp64"] for r in recs]
-    pair_evals = sum(a * pairs * R for a in applies)
-    value = job_value(pair_evals, world, elapsed)
+    pairs = sc.pair_count()
+    return dict(sc=sc, ctx=ctx, b=b, mu=mu, xh=xh, recs=recs, elapsed=elapsed, launches=launches, clocks=clk,
+                prof=prof, applies=applies, pair_evals=sum(a * pairs * R for a in applies), pairs=pairs,
+                tuning=tuning)
 
-    # accuracy of the mixed result against the plain FP64 GPU solve of the same scene
-    mu64 = torch.zeros_like(b)
-    ctx.solve(b, mu64, q.PREC_FP64, tol=1e-12)
-    rel_err = float(torch.linalg.norm(mu - mu64) / torch.linalg.norm(mu64))
 
-    # dominant kernel: self-block assembly (FP64 ALU) -- time it alone with events
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    ctx.assemble()
-    e1.record()
-    torch.cuda.synchronize()
-    asm_alone = e0.elapsed_time(e1) / 1e3
+def summary(w, steps, world):
+    recs = w["recs"]
+    step_ms = [r[0][0].elapsed_time(r[0][3]) for r in recs]
+    lat = sorted(step_ms)
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(math.ceil(p / 100 * len(lat))) - 1)]
+
+    st = recs[-1][1]
+    return {
+        "ms_per_step": w["elapsed"] / steps * 1e3,
+        "value": job_value(w["pair_evals"], world, w["elapsed"]),
+        "solves_per_s": steps * world / w["elapsed"],
+        "latency_ms": {"p50": pct(50), "p99": pct(99)},
+        "breakdown_ms": {"assembly": statistics.mean(r[0][0].elapsed_time(r[0][1]) for r in recs),
+                         "solve": statistics.mean(r[0][1].elapsed_time(r[0][2]) for r in recs),
+                         "far_field": statistics.mean(r[0][2].elapsed_time(r[0][3]) for r in recs)},
+        "solver": {"applies_per_solve": statistics.mean(w["applies"]), "iterations": st["iterations"],
+                   "refinements": st["refinements"], "fp64_accurate_applies": st["applies_fp64"],
+                   "rel_residual": st["rel_residual"]},
+    }
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2606_31380_b300 as q
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    clocks = ClockSampler(local_rank)
+    w = run_workload(q, torch, args.config, args.steps, args.warmup, args.tol, local_rank, dist, rank,
+                     profile=True, clocks=clocks)
+    sc, ctx, R, N = w["sc"], w["ctx"], w["sc"].n_rhs, w["ctx"].N
+    head = summary(w, args.steps, world)
+    acc = accuracy(q, torch, ctx, sc, w["b"], w["mu"], fp64_solve=N <= 40000)
+    clk = w["clocks"]
+    f_hz = (clk.get("sm_mhz") or 2032.0) * 1e6
+
+    # every profiled kernel of the timed region: launches, device time, share
+    prof = w["prof"]
+    t_all = w["elapsed"] * 1e3
+    kernels = {name: {"launches": n, "ms_total": ms, "ms_per_launch": ms / n if n else None,
+                      "share_of_step": ms / t_all} for name, (n, ms) in prof.items()}
+    pairs = w["pairs"]
+    # FP32 pair sum: CUDA-core kernel (one launch per group of up to 16 right-hand
+    # sides) or tensor-core kernel (one launch for all); whichever the autotuner chose
+    groups = 1 if R in (1, 2, 4, 8, 16) else len(range(0, R, 16))
+    for name, per_launch, peak_fn, bound in (
+            ("pairsum_f32_kernel", groups, pair_roofline, "alu (FP32 pipe + MUFU)"),
+            ("pairsum_tc_kernel", 1, pair_roofline_tc, "alu (MUFU; products on the tensor pipe)")):
+        n_l, ms_l = prof[name]
+        if n_l:
+            ach = n_l * pairs / per_launch / (ms_l / 1e3)
+            pk = peak_fn(sms, f_hz, R)
+            kernels[name].update({"bound": bound, "pairs_per_s": ach, "peak_pairs_per_s": pk, "frac": ach / pk})
+    nff, msff = prof["pairsum_ff_kernel"]
+    if nff:
+        aff = nff * pairs / (msff / 1e3)
+        pff = 128 * sms * f_hz / (FF_OPS_PER_PAIR + 72 * (R - 1))
+        kernels["pairsum_ff_kernel"].update({"bound": "alu (FP32 pipe)", "pairs_per_s": aff,
+                                             "peak_pairs_per_s": pff, "frac": aff / pff})
+    entries = sum(bd.n_nodes ** 2 for bd in sc.bodies)
+    hbm = measured_peaks()[0]["hbm_gbs"]
+    nb32, msb32 = prof["block_apply_kernel<float2>"]
+    if nb32:
+        gbs = nb32 * entries * 8 * ((R + 15) // 16) / (msb32 / 1e3) / 1e9
+        kernels["block_apply_kernel<float2>"].update({"bound": "hbm", "achieved_gbs": gbs, "peak_gbs": hbm,
+                                                      "frac": gbs / hbm})
+    ntc, mstc = prof["tc_block_kernel"]
+    if ntc:
+        # one launch per equal-size group streams every block once: 8 bytes (FP16 hi + lo) per complex entry
+        groups_b = len({bd.n_nodes for bd in sc.bodies})
+        gbs = ntc / groups_b * entries * 8 / (mstc / 1e3) / 1e9
+        kernels["tc_block_kernel"].update({"bound": "hbm", "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm})
+    na, msa = prof["selfblock_kernel"]
     asm_counts = ctx.assembly_counts()
     flops = assembly_flops(sc, asm_counts)
-    # FP64 peak from the unit counts: 2 FP64 lanes per clock per SM (the issue rate ncu
-    # reports for DFMA) x 2 FLOP x SMs x the maximum SM clock
-    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    peak64 = 2 * 2 * sms * 2.032e9 / 1e12
-    # cuBLAS DGEMM rate on this GPU (1.05 TFLOP/s when last measured); off by default so
-    # that the run's launch list holds only the library's own kernels
-    peak64_meas = fp64_peak_tflops(torch) if args.measure_fp64_peak else 1.05
+    peak64 = 2 * 2 * sms * f_hz / 1e12
+    peak64_meas = fp64_peak_tflops(torch) if not args.no_fp64_probe else None
+    if na:
+        a_tf = flops / (msa / 1e3 / args.steps) / 1e12  # one assembly per step
+        kernels["selfblock_kernel"].update({"bound": "alu (FP64 pipe)", "achieved_tflops": a_tf,
+                                            "peak_tflops": peak64, "frac": a_tf / peak64})
+    dominant = max(prof, key=lambda k: prof[k][1])
+    k_dom = kernels[dominant]
+    if dominant in ("pairsum_f32_kernel", "pairsum_tc_kernel"):
+        tag = "<%d>" % min(R, 16) if dominant == "pairsum_f32_kernel" else "<NH=%d>" % (16 if 2 * R <= 16 else 32)
+        note = ("min(128 FP32 lanes/clk/SM / (30+4R) ops, 16 MUFU/clk/SM / 4)" if dominant == "pairsum_f32_kernel"
+                else "min(128 FP32 lanes/clk/SM / 30 ops, 16 MUFU/clk/SM / 4): the 4R multiply-adds run on the "
+                     "tensor pipe")
+        roof = {"kernel": f"{dominant}{tag} (FP32 inter-body pair sum)", "bound": "alu",
+                "achieved": k_dom["pairs_per_s"], "peak": k_dom["peak_pairs_per_s"], "unit": "pair-interactions/s",
+                "frac": k_dom["frac"], "traffic": None,
+                "peak_note": "derived: %s pairs x %d SMs x %.0f MHz (median sampled SM clock)" % (note, sms, f_hz / 1e6)}
+    else:
+        roof = {"kernel": dominant, "bound": k_dom.get("bound"),
+                "achieved": k_dom.get("pairs_per_s") or k_dom.get("achieved_tflops") or k_dom.get("achieved_gbs"),
+                "peak": k_dom.get("peak_pairs_per_s") or k_dom.get("peak_tflops") or k_dom.get("peak_gbs"),
+                "frac": k_dom.get("frac"), "traffic": None,
+                "unit": "pair-interactions/s" if "pairs_per_s" in k_dom else "TFLOP/s" if "achieved_tflops" in k_dom
+                else "GB/s"}
+    kernels["note"] = ("device time of every launch in the timed region (CUDA events around each launch on its "
+                       "stream); peaks at the median sampled SM clock; HBM peak of %s" % measured_peaks()[1])
 
-    # FP32 apply pair rate (hot loop of the inner solver)
-    x32 = torch.randn((N, R), dtype=torch.complex64, device="cuda")
-    y32 = torch.empty_like(x32)
-    ctx.apply(x32, y32, q.PREC_FP32)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(5):
-        ctx.apply(x32, y32, q.PREC_FP32)
-    e1.record()
-    torch.cuda.synchronize()
-    apply_ms = e0.elapsed_time(e1) / 5
-
-    # the other hot kernels alone, each against its own roofline
-    kernels = kernel_rooflines(torch, q, ctx, sc, N, R, pairs, local_rank)
-
-    # e2e: through the C ABI from host descriptors to host results
-    e2e_steps = max(1, min(args.steps, 3))
+    # the same workload through the C ABI from host descriptors to host results
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    M = w["xh"].shape[0]
     mu_h = torch.empty((N, R), dtype=torch.complex128, pin_memory=True)
     u_h = torch.empty((M, R), dtype=torch.complex128, pin_memory=True)
     torch.cuda.synchronize()
@@ -362,13 +423,10 @@ def run_ours(args, rank, world, local_rank):
         c2 = q.Context(local_rank)
         c2.set_bodies(sc.bodies)
         c2.set_wavenumber(sc.k, sc.eta)
-        c2.assemble()
         bb = torch.zeros((N, R), dtype=torch.complex128, device="cuda")
-        c2.incident_plane(sc.directions, bb)
         mm = torch.zeros_like(bb)
-        st = c2.solve(bb, mm, q.PREC_FP32, tol=args.tol)
         uu = torch.zeros((M, R), dtype=torch.complex128, device="cuda")
-        c2.farfield(mm, xh, uu)
+        st = solve_step(q, c2, sc, bb, mm, uu, w["xh"], args.tol)
         mu_h.copy_(mm, non_blocking=True)
         u_h.copy_(uu, non_blocking=True)
         torch.cuda.synchronize()
@@ -378,52 +436,53 @@ def run_ours(args, rank, world, local_rank):
     h2d = sum(8 * (9 + 3 + 6 + len(bd.mode_cos) + len(bd.mode_sin)) for bd in sc.bodies) + 8 * 3 * R + 8 * 3 * M
     d2h = 16 * N * R + 16 * M * R
 
+    # the other workloads of the metric, a few solves each
+    extra = {}
+    if not args.no_extra:
+        for cfg, st_, wu in ((1, 5, 2), (2, 3, 1)):
+            if cfg == args.config:
+                continue
+            wx = run_workload(q, torch, cfg, st_, wu, args.tol, local_rank, dist, rank)
+            sx = summary(wx, st_, world)
+            sx["workload"] = wx["sc"].name
+            sx.update(accuracy(q, torch, wx["ctx"], wx["sc"], wx["b"], wx["mu"], fp64_solve=wx["ctx"].N <= 40000))
+            extra[f"config{cfg}"] = sx
+            wx["ctx"].close()
+            del wx
+            torch.cuda.empty_cache()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    ms = elapsed / args.steps * 1e3
-    lat = sorted(step_ms)
-
-    def pct(p):
-        return lat[min(len(lat) - 1, int(math.ceil(p / 100 * len(lat))) - 1)]
-
-    achieved = flops / asm_alone / 1e12
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64",
         "precision_note": ("f32 inner operator; f64 and float-float (pairs of f32) in the assembly, "
                            "refinement residual and far field; f64 Krylov basis"),
         "data": "synthetic (seeded quasi-axisymmetric bodies)",
         "config": {"workload": sc.name, "n_bodies": len(sc.bodies), "N": N, "R": R, "k": sc.k, "eta": sc.eta,
                    "tol": args.tol, "far_field_dirs": M, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (self blocks %.2f GB resident)" % (
-                       sum(bd.n_nodes ** 2 for bd in sc.bodies) * 24 / 1e9)},
-        "solves_per_s": args.steps * world / elapsed,
-        "latency_ms": {"p50": pct(50), "p99": pct(99)},
-        "breakdown_ms": {"assembly": statistics.mean(asm_ms), "solve": statistics.mean(solve_ms),
-                         "far_field": statistics.mean(ff_ms)},
-        "solver": {"applies_per_solve": statistics.mean(applies), "iterations": recs[-1][1]["iterations"],
-                   "refinements": recs[-1][1]["refinements"], "rel_residual": recs[-1][1]["rel_residual"],
-                   "rel_err_vs_fp64_gpu": rel_err},
-        "fp32_apply": {"ms": apply_ms, "pairs_per_s": pairs / (apply_ms / 1e3),
-                       "pair_rhs_per_s": pairs * R / (apply_ms / 1e3)},
+                   "l2": "inputs larger than L2 (self blocks %.2f GB resident)" % (entries * 24 / 1e9)},
+        "solves_per_s": head["solves_per_s"], "latency_ms": head["latency_ms"],
+        "breakdown_ms": head["breakdown_ms"], "solver": head["solver"], "accuracy": acc,
         "assembly_outer_nodes": {"modal": asm_counts[0], "far": asm_counts[1]},
-        "roofline": {"kernel": "selfblock_kernel (FP64 self-block assembly)", "bound": "alu",
-                     "achieved": achieved, "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64,
-                     "traffic": None,
-                     "peak_note": ("derived: 2 FP64 lanes/clk/SM x 2 FLOP x %d SMs x 2.032 GHz (nominal 1.25); "
-                                   "cuBLAS DGEMM %.3f TFLOP/s on this GPU%s"
-                                   % (sms, peak64_meas, "" if args.measure_fp64_peak else " (earlier measurement)"))},
-        "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches,
+        "roofline": roof,
+        "tuning": w["tuning"],
+        "fp64_peak": {"dgemm_tflops_measured": peak64_meas, "derived_tflops": peak64,
+                      "note": "cuBLAS DGEMM 8192^3 best of 5 in this run; derived = 2 lanes/clk/SM x 2 x SMs x clock"},
+        "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": w["launches"],
         "clocks": clk,
         "kernels": kernels,
+        "other_workloads": extra,
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     print(json.dumps(out), flush=True)
+    ctx.close()
     if dist:
         dist.destroy_process_group()
 
@@ -538,10 +597,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", type=int, default=1, help="workload index (1 = 16 bodies x 2048 nodes, k = 5)")
+    ap.add_argument("--config", type=int, default=3,
+                    help="workload index (3 = 1000 bodies x 512 nodes, k = 3, 4 RHS; 1 = 16 x 2048, 2 = 100 x 1152)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--measure-fp64-peak", action="store_true", help="time a cuBLAS DGEMM for the FP64 peak note")
+    ap.add_argument("--no-fp64-probe", action="store_true", help="skip the cuBLAS DGEMM that measures the FP64 peak")
+    ap.add_argument("--no-extra", action="store_true", help="measure the headline workload only")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--bodies", type=int, default=0, help="use only the first B bodies (small profiling case)")
     ap.add_argument("--tol", type=float, default=1e-10,
                     help="relative FP64 residual target of the mixed solve (the metric asks 1e-8 relative error)")

@@ -110,6 +110,65 @@ const char* qams_strerror(int code);
  * contexts); lets callers attribute device work to the library. */
 long long qams_kernel_launches(void);
 
+/* Launch timing of the hot kernels (a measurement hook; the paper has no
+ * counterpart).  While enabled, every launch of the kernels below is
+ * bracketed by two CUDA events on the stream it is launched on; read
+ * returns the number of launches timed and their summed device time since
+ * the last enable (blocking: waits for the recorded events).  Enabling
+ * again clears the sums; disabling stops recording.
+ * Errors: QAMS_EINVAL (NULL context or pointer, slot out of range), QAMS_ECUDA. */
+enum {
+  QAMS_PROF_PAIRSUM_FP32 = 0, /* inter-body pair sum, FP32 */
+  QAMS_PROF_PAIRSUM_FF = 1,   /* inter-body pair sum, float-float */
+  QAMS_PROF_PAIRSUM_FP64 = 2, /* inter-body pair sum, FP64 */
+  QAMS_PROF_BLOCK_FP32 = 3,   /* self-block / preconditioner products, complex64 */
+  QAMS_PROF_BLOCK_FP64 = 4,   /* self-block / preconditioner products, complex128 */
+  QAMS_PROF_ASSEMBLY = 5,     /* self-block assembly kernel */
+  QAMS_PROF_BLOCK_TC = 6,     /* self-block / preconditioner products on the tensor cores */
+  QAMS_PROF_PAIRSUM_TC = 7,   /* FP32 pair sum with its accumulation on the tensor cores */
+  QAMS_PROF_COUNT = 8
+};
+int qams_profile_enable(qams_ctx* ctx, int on);
+int qams_profile_read(qams_ctx* ctx, int slot, long long* launches, double* total_ms);
+
+/* Tuning options of a context (no counterpart in the paper: they choose
+ * between equivalent kernels and launch shapes, never the arithmetic's
+ * result beyond rounding).
+ *   QAMS_OPT_TC_MIN_RHS  FP32 self-block / preconditioner products run on
+ *                        the tensor cores when R >= value (default 8;
+ *                        17 = never).
+ *   QAMS_OPT_TC_PAIR_MIN_RHS  the FP32 pair sum accumulates on the tensor
+ *                        cores when R >= value (default 2; 17 = never).
+ * Errors: QAMS_EINVAL (NULL context or pointer, unknown key, value out of
+ * range). */
+enum { QAMS_OPT_TC_MIN_RHS = 0, QAMS_OPT_TC_PAIR_MIN_RHS = 1 };
+int qams_set_option(qams_ctx* ctx, int key, long long value);
+int qams_get_option(const qams_ctx* ctx, int key, long long* value);
+
+/* Launch-shape autotuner (no counterpart in the paper; every candidate
+ * computes the same sums up to rounding).  For R (1..16) right-hand sides on
+ * the context's bodies it times, with CUDA events on `stream`, the FP32 pair
+ * sum with its multiply-accumulate on the CUDA cores or on the tensor cores
+ * for each distinct source-split count (about 1, 2, 4, 8 and 16 CTAs per SM),
+ * and, after qams_assemble and for R >= 8, the FP32 self-block product on
+ * the CUDA cores or on the tensor cores.  The fastest choices are installed in the context
+ * (split tables; QAMS_OPT_TC_PAIR_MIN_RHS and QAMS_OPT_TC_MIN_RHS set so
+ * that R takes them) and cached for the process under (device, body sizes,
+ * R): a later call for the same shape installs the cached choice without
+ * timing (cached = 1).  Needs the bodies and the wavenumber.  Blocking.
+ * Errors: QAMS_EINVAL, QAMS_EBUDGET (scratch vectors), QAMS_ETIMEOUT,
+ * QAMS_ECUDA. */
+typedef struct {
+  int R;
+  int pair_tc;      /* 1: pair sum on the tensor cores */
+  int pair_splits;  /* source splits (grid rows) of the pair sum */
+  int block_tc;     /* 1: block products on the tensor cores; -1: not timed (no assembly) */
+  double pair_ms;   /* device time of one FP32 pair sum with the choice */
+  double block_ms;  /* device time of one FP32 self-block product with the choice */
+  int cached;       /* 1: taken from the process-wide cache */
+} qams_tuning;
+int qams_autotune(qams_ctx* ctx, int R, qams_tuning* out, void* stream);
+
 /* Create a context on CUDA device `cuda_device`.  hbm_budget_bytes = 0 means
  * no limit.  Errors: QAMS_EINVAL, QAMS_ECUDA. */
 int qams_create(qams_ctx** out, int cuda_device, size_t hbm_budget_bytes);

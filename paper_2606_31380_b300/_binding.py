@@ -13,6 +13,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 PREC_FP64 = 0
 PREC_FP32 = 1
 PREC_FF = 2  # float-float pair sum on complex128 data
+# launch-timing slots (qams_profile_read)
+PROF_PAIRSUM_FP32, PROF_PAIRSUM_FF, PROF_PAIRSUM_FP64, PROF_BLOCK_FP32, PROF_BLOCK_FP64, PROF_ASSEMBLY, \
+    PROF_BLOCK_TC, PROF_PAIRSUM_TC = range(8)
+OPT_TC_MIN_RHS, OPT_TC_PAIR_MIN_RHS = 0, 1  # qams_set_option keys
 
 
 def lib_path() -> str:
@@ -28,6 +32,11 @@ class SolveOpts(C.Structure):
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double),
                 ("solve_ms", C.c_double), ("applies_fp32", C.c_int), ("applies_fp64", C.c_int)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("R", C.c_int), ("pair_tc", C.c_int), ("pair_splits", C.c_int), ("block_tc", C.c_int),
+                ("pair_ms", C.c_double), ("block_ms", C.c_double), ("cached", C.c_int)]
 
 
 class Request(C.Structure):
@@ -96,6 +105,11 @@ def load_library():
         "qams_field": (i, [vp, i, vp, i, vp, vp, vp]),
         "qams_body_nodes": (i, [vp, vp, vp, vp]),
         "qams_selfblock_apply": (i, [vp, i, vp, vp, i, vp]),
+        "qams_profile_enable": (i, [vp, i]),
+        "qams_set_option": (i, [vp, i, ll]),
+        "qams_autotune": (i, [vp, i, C.POINTER(Tuning), vp]),
+        "qams_get_option": (i, [vp, i, C.POINTER(ll)]),
+        "qams_profile_read": (i, [vp, i, C.POINTER(ll), C.POINTER(d)]),
         "qams_precond_apply": (i, [vp, i, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
@@ -239,6 +253,31 @@ class Context:
         _check(self.lib.qams_pairsum(self._h, R, _dev(sigma, dt, (self.N, R), "sigma"),
                                      _dev(y, dt, (self.N, R), "y"), precision, C.c_void_p(_stream_ptr(stream))),
                "qams_pairsum")
+
+    def autotune(self, R: int, stream=None) -> dict:
+        """Time the equivalent FP32 kernel variants for R right-hand sides and
+        install the fastest (qams_autotune); returns the choice."""
+        t = Tuning()
+        _check(self.lib.qams_autotune(self._h, R, C.byref(t), C.c_void_p(_stream_ptr(stream))), "qams_autotune")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
+    def set_option(self, key: int, value: int):
+        _check(self.lib.qams_set_option(self._h, key, int(value)), "qams_set_option")
+
+    def get_option(self, key: int) -> int:
+        v = C.c_longlong()
+        _check(self.lib.qams_get_option(self._h, key, C.byref(v)), "qams_get_option")
+        return int(v.value)
+
+    def profile(self, on: bool):
+        """Start (clearing the sums) or stop timing the hot kernels' launches."""
+        _check(self.lib.qams_profile_enable(self._h, 1 if on else 0), "qams_profile_enable")
+
+    def profile_read(self, slot: int):
+        """(launches, total device ms) of one kernel class since profile(True)."""
+        n, ms = C.c_longlong(), C.c_double()
+        _check(self.lib.qams_profile_read(self._h, slot, C.byref(n), C.byref(ms)), "qams_profile_read")
+        return int(n.value), float(ms.value)
 
     def assemble(self, stream=None):
         _check(self.lib.qams_assemble(self._h, C.c_void_p(_stream_ptr(stream))), "qams_assemble")

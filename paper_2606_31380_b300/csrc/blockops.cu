@@ -100,6 +100,8 @@ void launch_block(qams_ctx* c, const void* blocks, const void* x, void* y, int R
 
 template <typename T2>
 void block_dispatch(qams_ctx* c, const void* blocks, const void* x, void* y, int R, int acc, cudaStream_t st) {
+  const int slot = sizeof(T2) == sizeof(double2) ? QAMS_PROF_BLOCK_FP64 : QAMS_PROF_BLOCK_FP32;
+  cudaEvent_t pe = qams_prof_begin(c, slot, st);
   for (int r0 = 0; r0 < R;) {
     const int left = R - r0;
     int rc = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
@@ -112,6 +114,7 @@ void block_dispatch(qams_ctx* c, const void* blocks, const void* x, void* y, int
     }
     r0 += rc;
   }
+  qams_prof_end(c, slot, st, pe);
 }
 
 }  // namespace
@@ -123,24 +126,44 @@ int qams_blocks_to_fp32(qams_ctx* c, cudaStream_t st) {
   const long long n = c->block_entries;
   to_fp32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2*)c->blocks64.p, (float2*)c->blocks32.p, n); qams_count_launch();
   QAMS_CUDA(cudaGetLastError());
-  return QAMS_OK;
+  // split copies for the tensor-core product (the preconditioner's follow its build)
+  c->tc_pinv_ok = false;
+  if ((rc = qams_tc_groups(c))) return rc;
+  return qams_tc_prepare(c, 0, st);
 }
 
+namespace {
+// The tensor-core product when it applies (FP32, enough right-hand sides,
+// split copy available); QAMS_EINVAL means "use the CUDA-core kernel".
+int try_tc(qams_ctx* c, const void* blocks, int R, const void* x, void* y, bool accumulate, cudaStream_t st) {
+  if (R < c->tc_min_r) return QAMS_EINVAL;
+  const int which = blocks == c->blocks32.p ? 0 : blocks == c->pinv32.p ? 1 : -1;
+  if (which < 0) return QAMS_EINVAL;
+  return qams_tc_block_apply(c, which, R, x, y, accumulate, st);
+}
+}  // namespace
+
 int qams_block_apply(qams_ctx* c, int R, const void* x, void* y, int precision, bool accumulate, cudaStream_t st) {
-  if (precision == QAMS_PREC_FP64)
+  if (precision == QAMS_PREC_FP64) {
     block_dispatch<double2>(c, c->blocks64.p, x, y, R, accumulate ? 1 : 0, st);
-  else
+  } else {
+    const int rc = try_tc(c, c->blocks32.p, R, x, y, accumulate, st);
+    if (rc != QAMS_EINVAL) return rc;
     block_dispatch<float2>(c, c->blocks32.p, x, y, R, accumulate ? 1 : 0, st);
+  }
   QAMS_CUDA(cudaGetLastError());
   return QAMS_OK;
 }
 
 int qams_block_apply_ptr(qams_ctx* c, const void* blocks, int R, const void* x, void* y, int precision,
                          bool accumulate, cudaStream_t st) {
-  if (precision == QAMS_PREC_FP64)
+  if (precision == QAMS_PREC_FP64) {
     block_dispatch<double2>(c, blocks, x, y, R, accumulate ? 1 : 0, st);
-  else
+  } else {
+    const int rc = try_tc(c, blocks, R, x, y, accumulate, st);
+    if (rc != QAMS_EINVAL) return rc;
     block_dispatch<float2>(c, blocks, x, y, R, accumulate ? 1 : 0, st);
+  }
   QAMS_CUDA(cudaGetLastError());
   return QAMS_OK;
 }

@@ -5,7 +5,11 @@
 
 #include "qams_internal.h"
 
+#include <algorithm>
 #include <atomic>
+#include <map>
+#include <string>
+#include <iterator>
 
 static thread_local char g_last_cuda[256];
 static std::atomic<long long> g_launches{0};
@@ -16,10 +20,62 @@ void qams_internal_last_cuda_error(cudaError_t e, const char* what) {
   snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", what, cudaGetErrorString(e));
 }
 
+void FitAlloc::init(size_t size) {
+  std::lock_guard<std::mutex> lk(mu_);
+  size_ = size & ~(size_t)255;
+  free_.clear();
+  if (size_) free_[0] = size_;
+}
+
+long long FitAlloc::alloc(size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  std::lock_guard<std::mutex> lk(mu_);
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second < bytes) continue;
+    const size_t off = it->first, len = it->second;
+    free_.erase(it);
+    if (len > bytes) free_[off + bytes] = len - bytes;
+    return (long long)off;
+  }
+  return -1;
+}
+
+void FitAlloc::release(size_t off, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  std::lock_guard<std::mutex> lk(mu_);
+  auto it = free_.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != free_.end() && it->first + it->second == nx->first) {  // merge with the next range
+    it->second += nx->second;
+    free_.erase(nx);
+  }
+  if (it != free_.begin()) {  // and with the previous one
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      free_.erase(it);
+    }
+  }
+}
+
+size_t FitAlloc::largest_free() {
+  std::lock_guard<std::mutex> lk(mu_);
+  size_t m = 0;
+  for (auto& f : free_) m = std::max(m, f.second);
+  return m;
+}
+
 int qams_dev_alloc(qams_ctx* c, DeviceBuf* b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (c->budget && c->allocated + bytes > c->budget) return QAMS_EBUDGET;
-  QAMS_CUDA(cudaMalloc(&b->p, bytes));
+  if (c->arena) {
+    // a serving reservation: no cudaMalloc (and no device synchronisation)
+    const long long off = c->arena->fa.alloc(bytes);
+    if (off < 0) return QAMS_EBUDGET;
+    b->p = c->arena->base + off;
+  } else {
+    QAMS_CUDA(cudaMalloc(&b->p, bytes));
+  }
   b->bytes = bytes;
   c->allocated += bytes;
   return QAMS_OK;
@@ -27,23 +83,109 @@ int qams_dev_alloc(qams_ctx* c, DeviceBuf* b, size_t bytes) {
 
 void qams_dev_free(qams_ctx* c, DeviceBuf* b) {
   if (b->p) {
-    cudaFree(b->p);
+    // in a reservation the range is reused by later work of the same request,
+    // which runs on the same stream after every kernel that read it
+    if (c->arena)
+      c->arena->fa.release((size_t)((char*)b->p - c->arena->base), b->bytes);
+    else
+      cudaFree(b->p);
     c->allocated -= b->bytes;
   }
   b->p = nullptr;
   b->bytes = 0;
 }
 
+cudaEvent_t qams_prof_begin(qams_ctx* c, int slot, cudaStream_t st) {
+  if (!c->prof || slot < 0 || slot >= QAMS_PROF_COUNT) return nullptr;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, st);
+  return e;
+}
+
+void qams_prof_end(qams_ctx* c, int slot, cudaStream_t st, cudaEvent_t start) {
+  if (!start) return;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaEventDestroy(start);
+    return;
+  }
+  cudaEventRecord(e, st);
+  c->prof_slots[slot].pending.push_back(start);
+  c->prof_slots[slot].pending.push_back(e);
+}
+
+static void prof_drain(qams_ctx* c) {
+  for (ProfSlot& ps : c->prof_slots) {
+    for (size_t i = 0; i + 1 < ps.pending.size(); i += 2) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(ps.pending[i + 1]) == cudaSuccess &&
+          cudaEventElapsedTime(&ms, ps.pending[i], ps.pending[i + 1]) == cudaSuccess) {
+        ps.ms += ms;
+        ps.launches += 1;
+      }
+      cudaEventDestroy(ps.pending[i]);
+      cudaEventDestroy(ps.pending[i + 1]);
+    }
+    ps.pending.clear();
+  }
+}
+
 qams_ctx::~qams_ctx() {
   cudaSetDevice(device);
+  prof_drain(this);
   for (DeviceBuf* b : {&x64, &n64, &x32, &n32, &x32lo, &n32lo, &centers, &boff, &jac64, &d_tiles, &d_splits, &partial,
-                        &blocks64, &blocks32, &blk_off, &ws_sigma, &ws_y, &pinv32, &pinv64})
+                        &blocks64, &blocks32, &blk_off, &ws_sigma, &ws_y, &pinv32, &pinv64, &tc_blk_hi, &tc_blk_lo,
+                        &tc_pinv_hi, &tc_pinv_lo, &tc_bt, &tc_amax, &tc_err})
     qams_dev_free(this, b);
 }
 
 extern "C" {
 
 long long qams_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int qams_set_option(qams_ctx* c, int key, long long value) {
+  if (!c) return QAMS_EINVAL;
+  switch (key) {
+    case QAMS_OPT_TC_MIN_RHS:
+      if (value < 1 || value > 17) return QAMS_EINVAL;
+      c->tc_min_r = (int)value;
+      return QAMS_OK;
+    case QAMS_OPT_TC_PAIR_MIN_RHS:
+      if (value < 1 || value > 17) return QAMS_EINVAL;
+      c->tc_pair_min_r = (int)value;
+      return QAMS_OK;
+    default: return QAMS_EINVAL;
+  }
+}
+
+int qams_get_option(const qams_ctx* c, int key, long long* value) {
+  if (!c || !value) return QAMS_EINVAL;
+  switch (key) {
+    case QAMS_OPT_TC_MIN_RHS: *value = c->tc_min_r; return QAMS_OK;
+    case QAMS_OPT_TC_PAIR_MIN_RHS: *value = c->tc_pair_min_r; return QAMS_OK;
+    default: return QAMS_EINVAL;
+  }
+}
+
+int qams_profile_enable(qams_ctx* c, int on) {
+  if (!c) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  prof_drain(c);
+  if (on)
+    for (ProfSlot& ps : c->prof_slots) ps = ProfSlot{};
+  c->prof = on != 0;
+  return QAMS_OK;
+}
+
+int qams_profile_read(qams_ctx* c, int slot, long long* launches, double* total_ms) {
+  if (!c || slot < 0 || slot >= QAMS_PROF_COUNT || !launches || !total_ms) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  prof_drain(c);
+  *launches = c->prof_slots[slot].launches;
+  *total_ms = c->prof_slots[slot].ms;
+  return QAMS_OK;
+}
 
 const char* qams_strerror(int code) {
   switch (code) {
@@ -96,10 +238,13 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
     }
   QAMS_CUDA(cudaSetDevice(c->device));
   for (DeviceBuf* b : {&c->x64, &c->n64, &c->x32, &c->n32, &c->x32lo, &c->n32lo, &c->centers, &c->boff, &c->jac64, &c->blocks64,
-                       &c->blocks32, &c->blk_off, &c->ws_sigma, &c->ws_y, &c->pinv32, &c->pinv64})
+                       &c->blocks32, &c->blk_off, &c->ws_sigma, &c->ws_y, &c->pinv32, &c->pinv64, &c->tc_blk_hi,
+                       &c->tc_blk_lo, &c->tc_pinv_hi, &c->tc_pinv_lo, &c->tc_bt})
     qams_dev_free(c, b);
   c->assembled = false;
   c->have_precond = false;
+  c->tc_blk_ok = c->tc_pinv_ok = false;
+  c->tc_groups.clear();
   c->bodies = std::move(bh);
   int rc = qams_build_nodes(c);
   if (rc) return rc;
@@ -139,8 +284,23 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
   if ((rc = qams_dev_alloc(c, &c->centers, sizeof(double) * 4 * nb))) return rc;
   if ((rc = qams_dev_alloc(c, &c->boff, sizeof(long long) * (nb + 1)))) return rc;
   if ((rc = qams_dev_alloc(c, &c->jac64, sizeof(double) * N))) return rc;
-  std::vector<long long> boffs(nb + 1, 0);
-  for (int b = 0; b < nb; ++b) boffs[b + 1] = boffs[b] + (long long)c->bodies[b].n * c->bodies[b].n;
+  // classes of congruent bodies; every body's block offset is its class's
+  c->body_class.assign(nb, 0);
+  c->class_rep.clear();
+  c->class_blk.clear();
+  std::map<std::string, int> cls;
+  long long blk = 0;
+  for (int b = 0; b < nb; ++b) {
+    auto ins = cls.emplace(qams_shape_key(c->bodies[b]), (int)c->class_rep.size());
+    if (ins.second) {
+      c->class_rep.push_back(b);
+      c->class_blk.push_back(blk);
+      blk += (long long)c->bodies[b].n * c->bodies[b].n;
+    }
+    c->body_class[b] = ins.first->second;
+  }
+  std::vector<long long> boffs(nb + 1, blk);
+  for (int b = 0; b < nb; ++b) boffs[b] = c->class_blk[c->body_class[b]];
   if ((rc = qams_dev_alloc(c, &c->blk_off, sizeof(long long) * (nb + 1)))) return rc;
   QAMS_CUDA(cudaMemcpy(c->blk_off.p, boffs.data(), sizeof(long long) * (nb + 1), cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->jac64.p, c->hj.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
@@ -213,8 +373,7 @@ int qams_assembly_counts(const qams_ctx* c, long long* counts) {
 
 int qams_copy_selfblock(const qams_ctx* c, int body, void* dst, void* stream) {
   if (!c || !c->assembled || body < 0 || body >= (int)c->bodies.size() || !dst) return QAMS_EINVAL;
-  long long off = 0;
-  for (int b = 0; b < body; ++b) off += (long long)c->bodies[b].n * c->bodies[b].n;
+  const long long off = c->class_blk[c->body_class[body]];
   const long long n = c->bodies[body].n;
   QAMS_CUDA(cudaSetDevice(c->device));
   QAMS_CUDA(cudaMemcpyAsync(dst, (const double2*)c->blocks64.p + off, sizeof(double2) * n * n,
@@ -234,8 +393,7 @@ int qams_build_preconditioner(qams_ctx* c, void* stream) {
 
 int qams_copy_preconditioner(const qams_ctx* c, int body, void* dst, void* stream) {
   if (!c || !c->have_precond || body < 0 || body >= (int)c->bodies.size() || !dst) return QAMS_EINVAL;
-  long long off = 0;
-  for (int b = 0; b < body; ++b) off += (long long)c->bodies[b].n * c->bodies[b].n;
+  const long long off = c->class_blk[c->body_class[body]];
   const long long n = c->bodies[body].n;
   QAMS_CUDA(cudaSetDevice(c->device));
   QAMS_CUDA(cudaMemcpyAsync(dst, (const double2*)c->pinv64.p + off, sizeof(double2) * n * n,

@@ -265,3 +265,23 @@ extern "C" int qams_body_nodes(const qams_body_desc* desc, double* x_host, doubl
   body_nodes_into(bc, x_host, n_host, w_host, nullptr);
   return QAMS_OK;
 }
+
+std::string qams_shape_key(const BodyCopy& bc) {
+  const qams_body_desc& d = bc.d;
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  const int ints[5] = {d.profile_kind, d.n_panels, d.order, d.n_theta, d.profile_kind == 1 ? d.n_terms : 0};
+  put(ints, sizeof(ints));
+  if (d.profile_kind == 0) {
+    const double v[3] = {d.base_radius, d.axis_length, d.curvature};
+    put(v, sizeof(v));
+    const int nm = (int)bc.a.size();
+    put(&nm, sizeof(nm));
+    put(bc.a.data(), sizeof(double) * bc.a.size());
+    put(bc.b.data(), sizeof(double) * bc.b.size());
+  } else {
+    put(bc.series.data(), sizeof(double) * bc.series.size());
+  }
+  put(bc.breaks.data(), sizeof(double) * bc.breaks.size());
+  return k;
+}

@@ -24,6 +24,7 @@ namespace {
 
 constexpr int TILE = 128;
 constexpr int CHUNK = 128;
+constexpr int BODY_BATCH = 32;  // source bodies whose body-pair constants are formed together
 constexpr float INV_2PI = 0.15915494309189535f;
 constexpr float TWO_PI_HI = 6.28318548202514648f;    // float(2 pi)
 constexpr float TWO_PI_LO = -1.7484555314695172e-7f;  // 2 pi - TWO_PI_HI
@@ -38,6 +39,8 @@ __global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
   __shared__ float4 sp[CHUNK];
   __shared__ float4 sq[CHUNK];
   __shared__ float2 ss[CHUNK][RC];
+  __shared__ float4 bdc[BODY_BATCH];  // per source body: dc = c_a - c_b (x, y, z), rho0
+  __shared__ float4 bph[BODY_BATCH];  // rho0^2, cos k rho0, sin k rho0
 
   const TargetTile tile = tiles[blockIdx.x];
   const SourceSplit split = splits[blockIdx.y];
@@ -45,23 +48,32 @@ __global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
   const bool active = tid < tile.count;
   const long long t = tile.start + (active ? tid : 0);
   const float4 xt = x32[t];
-  const qd4 ca = centers[tile.body];
   const float kf = (float)k, etaf = (float)eta;
 
   float2 tot[RC];
 #pragma unroll
   for (int r = 0; r < RC; ++r) tot[r] = make_float2(0.f, 0.f);
 
-  for (int b = split.begin; b < split.end; ++b) {
+  for (int bb = split.begin; bb < split.end; bb += BODY_BATCH) {
+    // the tile's targets share one body: its FP64 body-pair constants are
+    // formed once per CTA, one source body per lane of the first warp
+    __syncthreads();
+    if (tid < BODY_BATCH && bb + tid < split.end) {
+      const qd4 ca = centers[tile.body], cb = centers[bb + tid];
+      const double dcx = ca.x - cb.x, dcy = ca.y - cb.y, dcz = ca.z - cb.z;
+      const double rho0 = sqrt(dcx * dcx + dcy * dcy + dcz * dcz);
+      double s0d, c0d;
+      sincos(k * rho0, &s0d, &c0d);
+      bdc[tid] = make_float4((float)dcx, (float)dcy, (float)dcz, (float)rho0);
+      bph[tid] = make_float4((float)(rho0 * rho0), (float)c0d, (float)s0d, 0.f);
+    }
+    __syncthreads();
+  for (int b = bb; b < min(split.end, bb + BODY_BATCH); ++b) {
     if (b == tile.body) continue;
-    const qd4 cb = centers[b];
-    const double dcx = ca.x - cb.x, dcy = ca.y - cb.y, dcz = ca.z - cb.z;
-    const double rho0 = sqrt(dcx * dcx + dcy * dcy + dcz * dcz);
-    double s0d, c0d;
-    sincos(k * rho0, &s0d, &c0d);
-    const float fx = (float)dcx, fy = (float)dcy, fz = (float)dcz;
-    const float rho0f = (float)rho0;
-    const float r02 = (float)(rho0 * rho0);
+    const float4 dcv = bdc[b - bb], phv = bph[b - bb];
+    const float fx = dcv.x, fy = dcv.y, fz = dcv.z;
+    const float rho0f = dcv.w;
+    const float r02 = phv.x;
     const float At = fx * xt.x + fy * xt.y + fz * xt.z;
 
     float2 acc[RC];
@@ -114,12 +126,13 @@ __global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
         }
       }
     }
-    const float c0 = (float)c0d, s0f = (float)s0d;
+    const float c0 = phv.y, s0f = phv.z;
 #pragma unroll
     for (int r = 0; r < RC; ++r) {
       tot[r].x += c0 * acc[r].x - s0f * acc[r].y;
       tot[r].y += c0 * acc[r].y + s0f * acc[r].x;
     }
+  }
   }
   if (active) {
     const float inv4pi = 0.079577471545947668f;
@@ -217,6 +230,8 @@ __global__ void __launch_bounds__(TILE) pairsum_ff_kernel(
   __shared__ float4 snh[CHUNK], snl[CHUNK];  // n_s (hi / lo), .w = n_s.dc (hi / lo)
   __shared__ float4 ssg[CHUNK][RC];          // sigma: re hi, re lo, im hi, im lo
   __shared__ float4 tab[256];
+  __shared__ qd4 bdd[BODY_BATCH];      // per source body: dc (x, y, z), rho0
+  __shared__ double2 bcs[BODY_BATCH];  // cos k rho0, sin k rho0
 
   ff_phase_table_fill(tab);
   const TargetTile tile = tiles[blockIdx.x];
@@ -234,13 +249,29 @@ __global__ void __launch_bounds__(TILE) pairsum_ff_kernel(
 #pragma unroll
   for (int r = 0; r < RC; ++r) tot[r] = make_double2(0.0, 0.0);
 
-  for (int b = split.begin; b < split.end; ++b) {
+  for (int bb = split.begin; bb < split.end; bb += BODY_BATCH) {
+    // body-pair constants once per CTA (the tile's targets share one body)
+    __syncthreads();
+    if (tid < BODY_BATCH && bb + tid < split.end) {
+      const qd4 cb = centers[bb + tid];
+      const double dcx = ca.x - cb.x, dcy = ca.y - cb.y, dcz = ca.z - cb.z;
+      const double rho0 = sqrt(dcx * dcx + dcy * dcy + dcz * dcz);
+      double s0d, c0d;
+      sincos(k * rho0, &s0d, &c0d);
+      qd4 v;
+      v.x = dcx;
+      v.y = dcy;
+      v.z = dcz;
+      v.w = rho0;
+      bdd[tid] = v;
+      bcs[tid] = make_double2(c0d, s0d);
+    }
+    __syncthreads();
+  for (int b = bb; b < min(split.end, bb + BODY_BATCH); ++b) {
     if (b == tile.body) continue;
-    const qd4 cb = centers[b];
-    const double dcx = ca.x - cb.x, dcy = ca.y - cb.y, dcz = ca.z - cb.z;
-    const double rho0 = sqrt(dcx * dcx + dcy * dcy + dcz * dcz);
-    double s0d, c0d;
-    sincos(k * rho0, &s0d, &c0d);
+    const qd4 dv = bdd[b - bb];
+    const double dcx = dv.x, dcy = dv.y, dcz = dv.z, rho0 = dv.w;
+    const double c0d = bcs[b - bb].x, s0d = bcs[b - bb].y;
     const ff r0f = ff_from_double(rho0);
     const ff r02 = ff_from_double(rho0 * rho0);
     const ff At = ff_from_double(dcx * ((double)th.x + tl.x) + dcy * ((double)th.y + tl.y) +
@@ -316,6 +347,7 @@ __global__ void __launch_bounds__(TILE) pairsum_ff_kernel(
       tot[r].y += c0d * bacc[r].y + s0d * bacc[r].x;
     }
   }
+  }
   if (active) {
     const double inv4pi = 0.079577471545947667884;
     double2* o = out + split_stride * blockIdx.y + t * out_ld + out_r0;
@@ -384,14 +416,29 @@ int qams_pairsum_prepare(qams_ctx* c) {
     const BodyHost& bh = c->bodies[b];
     for (int s = 0; s < bh.n; s += TILE) c->tiles.push_back({b, std::min(TILE, bh.n - s), bh.offset + s});
   }
+  qams_dev_free(c, &c->d_tiles);
+  int rc = qams_dev_alloc(c, &c->d_tiles, sizeof(TargetTile) * c->tiles.size());
+  if (rc) return rc;
+  QAMS_CUDA(cudaMemcpy(c->d_tiles.p, c->tiles.data(), sizeof(TargetTile) * c->tiles.size(),
+                       cudaMemcpyHostToDevice));
+  return qams_pairsum_set_splits(c, qams_pairsum_default_splits(c, 8));
+}
+
+// Source splits for about mult x SMs CTAs (at least 1, at most one per body).
+int qams_pairsum_default_splits(const qams_ctx* c, int mult) {
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const long long want = 8LL * sms;  // CTAs for a couple of waves
+  const long long want = (long long)mult * sms;
+  const long long nt = std::max<long long>(1, (long long)c->tiles.size());
+  return (int)std::max(1LL, std::min<long long>((long long)c->bodies.size(), (want + nt - 1) / nt));
+}
+
+// S contiguous source-body ranges of about N/S nodes each, and the partial-sum
+// buffer they need (S > 1).  Blocking.
+int qams_pairsum_set_splits(qams_ctx* c, int S) {
   const int nb = (int)c->bodies.size();
-  int S = (int)std::max(1LL, std::min<long long>(nb, (want + (long long)c->tiles.size() - 1) /
-                                                         (long long)c->tiles.size()));
+  S = std::max(1, std::min(S, nb));
   c->splits.clear();
-  // contiguous body ranges with about N/S nodes each
   long long per = (c->N + S - 1) / S, acc = 0;
   int begin = 0;
   for (int b = 0; b < nb; ++b) {
@@ -401,20 +448,15 @@ int qams_pairsum_prepare(qams_ctx* c) {
       begin = b + 1;
     }
   }
-  qams_dev_free(c, &c->d_tiles);
   qams_dev_free(c, &c->d_splits);
-  qams_dev_free(c, &c->partial);
-  int rc = qams_dev_alloc(c, &c->d_tiles, sizeof(TargetTile) * c->tiles.size());
+  int rc = qams_dev_alloc(c, &c->d_splits, sizeof(SourceSplit) * c->splits.size());
   if (rc) return rc;
-  rc = qams_dev_alloc(c, &c->d_splits, sizeof(SourceSplit) * c->splits.size());
-  if (rc) return rc;
-  QAMS_CUDA(cudaMemcpy(c->d_tiles.p, c->tiles.data(), sizeof(TargetTile) * c->tiles.size(),
-                       cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(c->d_splits.p, c->splits.data(), sizeof(SourceSplit) * c->splits.size(),
                        cudaMemcpyHostToDevice));
-  if (c->splits.size() > 1) {
-    rc = qams_dev_alloc(c, &c->partial, sizeof(double2) * 16 * (size_t)c->N * c->splits.size());
-    if (rc) return rc;
+  const size_t need = c->splits.size() > 1 ? sizeof(double2) * 16 * (size_t)c->N * c->splits.size() : 0;
+  if (c->partial.bytes < need || (need == 0 && c->partial.p)) {
+    qams_dev_free(c, &c->partial);
+    if (need && (rc = qams_dev_alloc(c, &c->partial, need))) return rc;
   }
   return QAMS_OK;
 }
@@ -422,6 +464,22 @@ int qams_pairsum_prepare(qams_ctx* c) {
 int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int precision, cudaStream_t st) {
   const int S = (int)c->splits.size();
   dim3 grid((unsigned)c->tiles.size(), (unsigned)S);
+  if (precision == QAMS_PREC_FP32 && R >= c->tc_pair_min_r && R <= 16) {
+    // multiply-accumulate on the tensor cores, all right-hand sides in one launch
+    float2* out = S > 1 ? (float2*)c->partial.p : (float2*)y;
+    cudaEvent_t pe = qams_prof_begin(c, QAMS_PROF_PAIRSUM_TC, st);
+    int rc = qams_pairsum_tc_launch(c, R, sigma, out, S > 1 ? c->N * R : 0, R, st);
+    qams_prof_end(c, QAMS_PROF_PAIRSUM_TC, st, pe);
+    if (rc) return rc;
+    if (S > 1) {
+      const long long n = c->N * R;
+      reduce_splits_kernel<float2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float2*)c->partial.p, S, c->N,
+                                                                              R, (float2*)y, R, 0);
+      qams_count_launch();
+      QAMS_CUDA(cudaGetLastError());
+    }
+    return QAMS_OK;
+  }
   for (int r0 = 0; r0 < R;) {
     const int rc = pick_rc(R - r0);
     if (precision == QAMS_PREC_FP32) {
@@ -429,6 +487,7 @@ int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int prec
       const long long stride = S > 1 ? c->N * rc : 0;
       const int ld = S > 1 ? rc : R, or0 = S > 1 ? 0 : r0;
       const float2* sg = (const float2*)sigma;
+      cudaEvent_t pe = qams_prof_begin(c, QAMS_PROF_PAIRSUM_FP32, st);
       switch (rc) {
         case 16: launch_f32<16>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
         case 8: launch_f32<8>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
@@ -436,6 +495,7 @@ int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int prec
         case 2: launch_f32<2>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
         default: launch_f32<1>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
       }
+      qams_prof_end(c, QAMS_PROF_PAIRSUM_FP32, st, pe);
       QAMS_CUDA(cudaGetLastError());
       if (S > 1) {
         const long long n = c->N * rc;
@@ -448,6 +508,8 @@ int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int prec
       const long long stride = S > 1 ? c->N * rc : 0;
       const int ld = S > 1 ? rc : R, or0 = S > 1 ? 0 : r0;
       const double2* sg = (const double2*)sigma;
+      const int slot = precision == QAMS_PREC_FF ? QAMS_PROF_PAIRSUM_FF : QAMS_PROF_PAIRSUM_FP64;
+      cudaEvent_t pe = qams_prof_begin(c, slot, st);
       if (precision == QAMS_PREC_FF) {
         switch (rc) {
           case 16: launch_ff<16>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
@@ -465,6 +527,7 @@ int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int prec
           default: launch_f64<1>(c, grid, sg, R, r0, out, stride, ld, or0, st); break;
         }
       }
+      qams_prof_end(c, slot, st, pe);
       QAMS_CUDA(cudaGetLastError());
       if (S > 1) {
         const long long n = c->N * rc;

@@ -10,13 +10,13 @@
 //   W -= C R                            (GEMM, rank-b update of the whole matrix)
 //   T = -C P                            (GEMM)
 //   W_k,: = R,  W_:,k = T,  W_kk = P    (own kernel)
-// after which W = A_b^{-1}.  The GEMMs are plain cuBLAS complex64 GEMMs,
-// batched over bodies of equal size.  Pivoting is local to the diagonal
+// after which W = A_b^{-1}.  The three products run in an own tiled
+// complex64 GEMM kernel (64 x 64 output tiles, 16-wide K chunks staged in
+// shared memory, 4 x 4 complex outputs per thread), batched over bodies of
+// equal size in one launch per product.  Pivoting is local to the diagonal
 // blocks; the self blocks of the second-kind combined-field operator
 // (1/2 I plus a smoothing part) keep them well conditioned, and a
 // vanishing pivot is reported as QAMS_ENUMERIC.
-#include <cublas_v2.h>
-
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -121,25 +121,101 @@ __global__ void fix_kernel(float2* const* __restrict__ W, int n, int k0, int b, 
   }
 }
 
+// One GEMM operand per batch entry z: tab[z] + off when a pointer table is
+// given, else base + z * bstride + off; row-major with leading dimension ld.
+struct Opnd {
+  float2* const* tab;
+  float2* base;
+  long long off, bstride;
+  int ld;
+};
+
+__device__ __forceinline__ float2* opnd_ptr(const Opnd& o, int z) {
+  return o.tab ? o.tab[z] + o.off : o.base + (long long)z * o.bstride + o.off;
+}
+
+constexpr int GT = 64;  // output tile (rows and columns)
+constexpr int GK = 16;  // K chunk
+
+// D = alpha A B (+ D when accumulate) for complex64 row-major A (M x K),
+// B (K x N), D (M x N); grid (N tiles, M tiles, batch).
+__global__ void __launch_bounds__(256) cgemm_kernel(Opnd A, Opnd B, Opnd D, int M, int N, int K, float2 alpha,
+                                                    int accumulate) {
+  __shared__ float2 As[GK][GT + 1];
+  __shared__ float2 Bs[GK][GT];
+  const int z = blockIdx.z;
+  const float2* a = opnd_ptr(A, z);
+  const float2* b = opnd_ptr(B, z);
+  float2* d = opnd_ptr(D, z);
+  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += GK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = t + 256 * q;
+      const int am = idx >> 4, ak = idx & 15;  // A tile: 64 rows x 16
+      As[ak][am] = (m0 + am < M && k0 + ak < K) ? a[(long long)(m0 + am) * A.ld + k0 + ak] : make_float2(0.f, 0.f);
+      const int bk = idx >> 6, bn = idx & 63;  // B tile: 16 rows x 64
+      Bs[bk][bn] = (k0 + bk < K && n0 + bn < N) ? b[(long long)(k0 + bk) * B.ld + n0 + bn] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+      float2 av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fmaf(av[i].x, bv[j].x, fmaf(-av[i].y, bv[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(av[i].x, bv[j].y, fmaf(av[i].y, bv[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      float2* o = d + (long long)m * D.ld + n;
+      float2 v = make_float2(alpha.x * acc[i][j].x - alpha.y * acc[i][j].y,
+                             alpha.x * acc[i][j].y + alpha.y * acc[i][j].x);
+      if (accumulate) {
+        v.x += o->x;
+        v.y += o->y;
+      }
+      *o = v;
+    }
+  }
+}
+
+void cgemm(const Opnd& A, const Opnd& B, const Opnd& D, int M, int N, int K, float2 alpha, int accumulate, int G,
+           cudaStream_t st) {
+  const dim3 grid((unsigned)((N + GT - 1) / GT), (unsigned)((M + GT - 1) / GT), (unsigned)G);
+  cgemm_kernel<<<grid, 256, 0, st>>>(A, B, D, M, N, K, alpha, accumulate);
+  qams_count_launch();
+}
+
 __global__ void widen_blocks_kernel(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) b[i] = make_double2(a[i].x, a[i].y);
 }
 
-#define QAMS_CUBLAS(call)                                        \
-  do {                                                           \
-    cublasStatus_t s_ = (call);                                  \
-    if (s_ != CUBLAS_STATUS_SUCCESS) {                           \
-      qams_internal_last_cuda_error(cudaErrorUnknown, #call);    \
-      rc = QAMS_ECUDA;                                           \
-      goto done;                                                 \
-    }                                                            \
-  } while (0)
-
 }  // namespace
 
 int qams_precond_launch(qams_ctx* c, cudaStream_t st) {
-  const int nb = (int)c->bodies.size();
   int rc = QAMS_OK;
   qams_dev_free(c, &c->pinv32);
   qams_dev_free(c, &c->pinv64);
@@ -147,26 +223,20 @@ int qams_precond_launch(qams_ctx* c, cudaStream_t st) {
   if ((rc = qams_dev_alloc(c, &c->pinv64, sizeof(double2) * (size_t)c->block_entries))) return rc;
   QAMS_CUDA(cudaMemcpyAsync(c->pinv32.p, c->blocks32.p, sizeof(float2) * (size_t)c->block_entries,
                             cudaMemcpyDeviceToDevice, st));
-  // group bodies by size
+  // one inverse per class of congruent bodies, grouped by size
   std::map<int, std::vector<int>> groups;
-  std::vector<long long> boff(nb);
-  long long off = 0;
-  for (int b = 0; b < nb; ++b) {
-    boff[b] = off;
-    off += (long long)c->bodies[b].n * c->bodies[b].n;
-    groups[c->bodies[b].n].push_back(b);
+  std::vector<long long> boff(c->class_rep.size());
+  for (size_t k = 0; k < c->class_rep.size(); ++k) {
+    boff[k] = c->class_blk[k];
+    groups[c->bodies[c->class_rep[k]].n].push_back((int)k);
   }
-  cublasHandle_t h = nullptr;
   DeviceBuf ptrs, Rb, Cb, Tb, Pb, stat;
   size_t maxg = 0, maxn = 0;
-  if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return QAMS_ECUDA;
-  cublasSetStream(h, st);
-  cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST);
   for (auto& g : groups) {
     maxg = std::max(maxg, g.second.size());
     maxn = std::max(maxn, (size_t)g.first);
   }
-  if ((rc = qams_dev_alloc(c, &ptrs, sizeof(void*) * 6 * maxg))) goto done;
+  if ((rc = qams_dev_alloc(c, &ptrs, sizeof(void*) * maxg))) goto done;
   if ((rc = qams_dev_alloc(c, &Rb, sizeof(float2) * maxg * BW * maxn))) goto done;
   if ((rc = qams_dev_alloc(c, &Cb, sizeof(float2) * maxg * BW * maxn))) goto done;
   if ((rc = qams_dev_alloc(c, &Tb, sizeof(float2) * maxg * BW * maxn))) goto done;
@@ -178,27 +248,17 @@ int qams_precond_launch(qams_ctx* c, cudaStream_t st) {
   for (auto& g : groups) {
     const int n = g.first;
     const int G = (int)g.second.size();
-    // pointer table: W[body], then per-body pointers of the GEMM operands
-    std::vector<void*> hp(6 * (size_t)G);
+    // pointer table of the group's matrices W (fixed for the whole elimination)
+    std::vector<float2*> hp((size_t)G);
     for (int q = 0; q < G; ++q) hp[q] = (float2*)c->pinv32.p + boff[g.second[q]];
     float2** dW = (float2**)ptrs.p;
-    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f),
-                    mone = make_cuComplex(-1.f, 0.f);
+    if (cudaMemcpyAsync(ptrs.p, hp.data(), sizeof(float2*) * G, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = QAMS_ECUDA;
+      goto done;
+    }
     for (int k0 = 0; k0 < n; k0 += BW) {
       const int b = std::min(BW, n - k0);
-      for (int q = 0; q < G; ++q) {
-        float2* W = (float2*)hp[q];
-        hp[G + q] = W + (long long)k0 * n;                 // W_k,: (row-major b x n)
-        hp[2 * G + q] = (float2*)Rb.p + (long long)q * b * n;
-        hp[3 * G + q] = (float2*)Cb.p + (long long)q * n * b;
-        hp[4 * G + q] = (float2*)Pb.p + (long long)q * b * b;
-        hp[5 * G + q] = (float2*)Tb.p + (long long)q * n * b;
-      }
-      if (cudaMemcpyAsync(ptrs.p, hp.data(), sizeof(void*) * 6 * G, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-        rc = QAMS_ECUDA;
-        goto done;
-      }
-      if (cudaStreamSynchronize(st) != cudaSuccess) { rc = QAMS_ECUDA; goto done; }  // hp is rewritten next step
       pivot_inverse_kernel<<<G, 256, sizeof(float2) * b * 2 * b, st>>>(dW, n, k0, b, (float2*)Pb.p, (int*)stat.p);
       qams_count_launch();
       {
@@ -206,27 +266,15 @@ int qams_precond_launch(qams_ctx* c, cudaStream_t st) {
         copy_col_block_kernel<<<dim3((unsigned)((nbk + 255) / 256), G), 256, 0, st>>>(dW, n, k0, b, (float2*)Cb.p);
         qams_count_launch();
       }
-      {
-        // column-major views: R^T (n x b) = W_k,:^T (n x b, ld n) * P^T (b x b, ld b)
-        const cuComplex** A = (const cuComplex**)(dW + G);
-        const cuComplex** B = (const cuComplex**)(dW + 4 * G);
-        cuComplex** Cc = (cuComplex**)(dW + 2 * G);
-        QAMS_CUBLAS(cublasCgemmBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, n, b, b, &one, A, n, B, b, &zero, Cc, n, G));
-      }
-      {
-        // W^T (n x n) -= R^T (n x b, ld n) * C^T (b x n, ld b)
-        const cuComplex** A = (const cuComplex**)(dW + 2 * G);
-        const cuComplex** B = (const cuComplex**)(dW + 3 * G);
-        cuComplex** Cc = (cuComplex**)dW;
-        QAMS_CUBLAS(cublasCgemmBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, n, n, b, &mone, A, n, B, b, &one, Cc, n, G));
-      }
-      {
-        // T^T (b x n, ld b) = -P^T (b x b) * C^T (b x n, ld b)
-        const cuComplex** A = (const cuComplex**)(dW + 4 * G);
-        const cuComplex** B = (const cuComplex**)(dW + 3 * G);
-        cuComplex** Cc = (cuComplex**)(dW + 5 * G);
-        QAMS_CUBLAS(cublasCgemmBatched(h, CUBLAS_OP_N, CUBLAS_OP_N, b, n, b, &mone, A, b, B, b, &zero, Cc, b, G));
-      }
+      const Opnd Wk{dW, nullptr, (long long)k0 * n, 0, n};              // W_k,: (b x n, ld n)
+      const Opnd Wf{dW, nullptr, 0, 0, n};                              // W (n x n)
+      const Opnd Ro{nullptr, (float2*)Rb.p, 0, (long long)b * n, n};   // R (b x n)
+      const Opnd Co{nullptr, (float2*)Cb.p, 0, (long long)n * b, b};   // C (n x b)
+      const Opnd Po{nullptr, (float2*)Pb.p, 0, (long long)b * b, b};   // P (b x b)
+      const Opnd To{nullptr, (float2*)Tb.p, 0, (long long)n * b, b};   // T (n x b)
+      cgemm(Po, Wk, Ro, b, n, b, make_float2(1.f, 0.f), 0, G, st);   // R = P W_k,:
+      cgemm(Co, Ro, Wf, n, n, b, make_float2(-1.f, 0.f), 1, G, st);  // W -= C R
+      cgemm(Co, Po, To, n, b, b, make_float2(-1.f, 0.f), 0, G, st);  // T = -C P
       {
         const long long nbk = (long long)n * b;
         fix_kernel<<<dim3((unsigned)((nbk + 255) / 256), G), 256, 0, st>>>(dW, n, k0, b, (const float2*)Rb.p,
@@ -249,8 +297,8 @@ int qams_precond_launch(qams_ctx* c, cudaStream_t st) {
     }
     if (hs) rc = QAMS_ENUMERIC;
   }
+  if (rc == QAMS_OK) rc = qams_tc_prepare(c, 1, st);  // split copy for the tensor-core product
 done:
-  if (h) cublasDestroy(h);
   for (DeviceBuf* b : {&ptrs, &Rb, &Cb, &Tb, &Pb, &stat}) qams_dev_free(c, b);
   return rc;
 }

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -44,6 +46,10 @@ int qams_copy_body(const qams_body_desc& src, BodyCopy* out);
 // while `bc` lives and is not moved).
 qams_body_desc qams_desc_view(const BodyCopy& bc);
 
+// The reference shape and discretisation of a body (everything but its
+// rotation and centre): congruent bodies have equal keys and one self block.
+std::string qams_shape_key(const BodyCopy& bc);
+
 struct BodyHost : BodyCopy {
   long long offset = 0;  // first node
   int n = 0;             // nodes
@@ -66,6 +72,45 @@ struct DeviceBuf {
   size_t bytes = 0;
 };
 
+// First-fit allocator over [0, size) with coalescing of freed neighbours;
+// offsets and lengths are multiples of 256 bytes.  Thread-safe.
+class FitAlloc {
+ public:
+  void init(size_t size);
+  long long alloc(size_t bytes);  // offset, or -1 when no free range fits
+  void release(size_t off, size_t bytes);
+  size_t size() const { return size_; }
+  size_t largest_free();
+
+ private:
+  size_t size_ = 0;
+  std::map<size_t, size_t> free_;  // offset -> length
+  std::mutex mu_;
+};
+
+// Device memory region handed to a context: qams_dev_alloc/free draw from
+// it instead of cudaMalloc/cudaFree (a serving slot's reservation).
+struct DevArena {
+  char* base = nullptr;
+  FitAlloc fa;
+};
+
+// Per-launch device times of the hot kernels (CUDA events on the launching
+// stream), recorded while profiling is switched on (qams_profile_enable).
+struct ProfSlot {
+  long long launches = 0;
+  double ms = 0.0;
+  std::vector<cudaEvent_t> pending;  // start/stop pairs not yet read
+};
+
+// A contiguous run of equal-size bodies: one tensor map per operand in the
+// tensor-core block product.
+struct TcGroup {
+  int first, nb, n;    // first body, bodies, nodes per body
+  long long node0;     // first node of the first body
+  long long elem0;     // first complex block entry of the first body
+};
+
 struct qams_ctx {
   int device = 0;
   size_t budget = 0;
@@ -75,6 +120,7 @@ struct qams_ctx {
   double k = 0.0, eta = 1.0;
   bool have_k = false;
   const int* cancel = nullptr;  // set by the server: checked between GMRES restart cycles
+  DevArena* arena = nullptr;    // set by the server: device memory comes from the request's reservation
 
   // host node tables (FP64, world frame)
   std::vector<double> hx, hn, hw, hj;  // [N][3], [N][3], [N], [N] (|J|)
@@ -90,7 +136,13 @@ struct qams_ctx {
   DeviceBuf boff;    // long long [nb+1]
   DeviceBuf jac64;   // double [N]: |J| at the nodes
 
-  // self blocks (row-major n_b x n_b per body, bodies back to back)
+  // congruent bodies share a self block (Sec. 4: D_tt computed once for
+  // identical bodies): body_class[b] = index into class_rep, the first body
+  // of each class; class_blk[k] = first block entry of class k
+  std::vector<int> body_class, class_rep;
+  std::vector<long long> class_blk;
+
+  // self blocks (row-major n_b x n_b per class of congruent bodies, back to back)
   DeviceBuf blocks64;  // complex128
   DeviceBuf blocks32;  // complex64 copy for the FP32 path
   DeviceBuf blk_off;   // long long [nb+1]: first entry of each block
@@ -106,6 +158,19 @@ struct qams_ctx {
   // apply workspaces
   DeviceBuf ws_sigma, ws_y;
 
+  // tensor-core block products (tc_block.cu): FP16 hi/lo split copies of the
+  // complex64 blocks, B-tile workspace, column maxima, timeout flag
+  std::vector<TcGroup> tc_groups;
+  DeviceBuf tc_blk_hi, tc_blk_lo, tc_pinv_hi, tc_pinv_lo, tc_bt, tc_amax, tc_err;
+  bool tc_blk_ok = false, tc_pinv_ok = false;
+  int tc_bt_R = -1;
+  int tc_min_r = 8;       // right-hand sides from which the FP32 block products use the tensor cores
+  int tc_pair_min_r = 2;  // ... and from which the FP32 pair sum accumulates on them
+
+  // launch timing of the hot kernels (QAMS_PROF_* slots of qams.h)
+  bool prof = false;
+  ProfSlot prof_slots[8];
+
   // pair-sum launch tables
   std::vector<TargetTile> tiles;
   std::vector<SourceSplit> splits;
@@ -114,6 +179,10 @@ struct qams_ctx {
 
   ~qams_ctx();
 };
+
+// Bracket one kernel launch with events when profiling is on (slot = QAMS_PROF_*).
+cudaEvent_t qams_prof_begin(qams_ctx* c, int slot, cudaStream_t st);
+void qams_prof_end(qams_ctx* c, int slot, cudaStream_t st, cudaEvent_t start);
 
 int qams_dev_alloc(qams_ctx* c, DeviceBuf* b, size_t bytes);
 void qams_dev_free(qams_ctx* c, DeviceBuf* b);
@@ -125,6 +194,8 @@ void qams_gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 // pairsum.cu
 int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int precision, cudaStream_t st);
 int qams_pairsum_prepare(qams_ctx* c);
+int qams_pairsum_set_splits(qams_ctx* c, int S);
+int qams_pairsum_default_splits(const qams_ctx* c, int mult);
 
 // selfblock.cu
 int qams_assemble_launch(qams_ctx* c, cudaStream_t st);
@@ -138,6 +209,16 @@ int qams_block_apply_ptr(qams_ctx* c, const void* blocks, int R, const void* x, 
 
 // precond.cu
 int qams_precond_launch(qams_ctx* c, cudaStream_t st);
+
+// tc_block.cu
+int qams_tc_groups(qams_ctx* c);
+int qams_tc_prepare(qams_ctx* c, int which, cudaStream_t st);
+int qams_tc_block_apply(qams_ctx* c, int which, int R, const void* x, void* y, bool accumulate, cudaStream_t st);
+int qams_tc_check(qams_ctx* c, cudaStream_t st);
+
+// tc_pairsum.cu
+int qams_pairsum_tc_launch(qams_ctx* c, int R, const void* sigma, void* out, long long split_stride, int out_ld,
+                           cudaStream_t st);
 
 // fields.cu
 int qams_incident_launch(qams_ctx* c, int R, const double* dirs_host, void* rhs, cudaStream_t st);

@@ -93,8 +93,9 @@ struct AsmBody {
   int ser, brk;       // table offsets: kind-1 series [4][n_terms][3], panel breaks [n_panels+1]
   double base, L, kappa;
   double a[8], b[8];
-  long long offset;
-  long long blk;   // first entry of the body's self block
+  long long offset;  // first node of the body
+  long long crow;    // first row of the body among the assembled rows
+  long long blk;     // first entry of the body's self block
   int n1, M;       // smooth-factor bandwidth and cosine-DFT size
   int rule;        // offset of the order's rule tables
 };
@@ -426,13 +427,15 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   double* bdq = bq + BATCH * pstride;
   float4* accD = reinterpret_cast<float4*>(bdq + BATCH * pstride);
 
-  const long long g = row0 + blockIdx.x;  // global target node
+  // rows of the assembled bodies (one per class of congruent bodies), back to back
+  const long long gc = row0 + blockIdx.x;
   int lo = 0, hi = nb - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (bodies[mid].offset <= g) lo = mid; else hi = mid - 1;
+    if (bodies[mid].crow <= gc) lo = mid; else hi = mid - 1;
   }
   const AsmBody B = bodies[lo];
+  const long long g = B.offset + (gc - B.crow);  // global target node
   const int tid = threadIdx.x;
   const int nth = B.n_theta, N = nth / 2, order = B.order;
   const int per_panel = order * nth;
@@ -846,15 +849,16 @@ size_t qams_selfblock_smem(int max_per_panel, int pstride) {
 }
 
 int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
-  const int nb = (int)c->bodies.size();
+  // one block per class of congruent bodies, from its first body's rows
+  const int nb = (int)c->class_rep.size();
   // rule tables per distinct order
   std::vector<double> rules;
   std::vector<int> rule_off(64, -1);
   std::vector<AsmBody> ab(nb);
-  long long blk = 0;
+  long long blk = 0, rows = 0;
   int max_nb = 0, pstride = 0;
   for (int b = 0; b < nb; ++b) {
-    const BodyHost& bh = c->bodies[b];
+    const BodyHost& bh = c->bodies[c->class_rep[b]];
     const qams_body_desc& d = bh.d;
     if (d.order > MAXORD || d.n_theta / 2 > MAXN) return QAMS_EINVAL;
     if (rule_off[d.order] < 0) {
@@ -915,6 +919,8 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
       A.b[m] = m < A.n_modes ? bh.b[m] : 0.0;
     }
     A.offset = bh.offset;
+    A.crow = rows;
+    rows += bh.n;
     A.blk = blk;
     blk += (long long)bh.n * bh.n;
     const double rmax = bh.rmax;
@@ -947,13 +953,15 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   const long long chunk = 1 << 20;
-  for (long long r0 = 0; r0 < c->N; r0 += chunk) {
-    const long long n = std::min(chunk, c->N - r0);
+  for (long long r0 = 0; r0 < rows; r0 += chunk) {
+    const long long n = std::min(chunk, rows - r0);
+    cudaEvent_t pe = qams_prof_begin(c, QAMS_PROF_ASSEMBLY, st);
     selfblock_kernel<<<(unsigned)n, NT, smem, st>>>((const AsmBody*)d_bodies.p, nb, (const double*)d_rules.p,
                                                     (const qd4*)c->x64.p, (const qd4*)c->n64.p,
                                                     (const double*)c->jac64.p, c->k, c->eta, r0,
                                                     (double2*)c->blocks64.p, (unsigned long long*)d_counts.p,
                                                     pstride); qams_count_launch();
+    qams_prof_end(c, QAMS_PROF_ASSEMBLY, st, pe);
     QAMS_CUDA(cudaGetLastError());
   }
   QAMS_CUDA(cudaStreamSynchronize(st));

@@ -1,5 +1,14 @@
 // Serving loop: admission by device footprint, one stream and one library
 // context per admitted request, requests overlapping on the device.
+//
+// Device memory: one pool of the server's budget is allocated when the
+// server starts.  Admitting a request reserves a contiguous region of its
+// footprint in the pool (first fit); the request's context draws every
+// buffer from that region (qams_dev_alloc), so serving makes no cudaMalloc
+// or cudaFree -- neither of which could overlap with other requests' work,
+// since both synchronise the device -- and an admitted request cannot run
+// out of memory through fragmentation.  A request whose footprint fits the
+// budget but finds no free region of that size waits in the queue.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,6 +19,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -21,6 +31,7 @@ using Clock = std::chrono::steady_clock;
 
 struct Req {
   uint64_t ticket = 0;
+  long long region = -1;  // offset of its reservation in the pool
   std::vector<qams_body_desc> bodies;
   std::vector<BodyCopy> copies;  // owns the arrays `bodies` points into
   std::vector<double> dirs, far_dirs;
@@ -41,6 +52,8 @@ double ms(Clock::time_point a, Clock::time_point b) {
 struct qams_server {
   int device = 0;
   size_t budget = 0, in_use = 0;
+  char* pool = nullptr;  // the whole budget, allocated at start
+  FitAlloc regions;      // reservations of running requests
   int slots = 1, running = 0;
   bool stop = false;
   uint64_t next = 1;
@@ -59,6 +72,8 @@ void qams_server::run(Req& q) {
   qams_ctx* c = nullptr;
   cudaStream_t st = nullptr;
   void *rhs = nullptr, *mu = nullptr, *uinf = nullptr;
+  DeviceBuf b_rhs, b_mu, b_uinf;
+  DevArena arena;  // outlives the context: its buffers go back here on destroy
   int rc = QAMS_OK;
   const int R = q.r.R, M = q.r.M;
   do {
@@ -66,12 +81,17 @@ void qams_server::run(Req& q) {
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { rc = QAMS_ECUDA; break; }
     if ((rc = qams_create(&c, device, 0))) break;
     c->cancel = &q.cancel;
+    arena.base = pool + q.region;
+    arena.fa.init(q.footprint);
+    c->arena = &arena;
     if ((rc = qams_set_bodies(c, (int)q.bodies.size(), q.bodies.data(), 0.0))) break;
     res.n_nodes = c->N;
     if ((rc = qams_set_wavenumber(c, q.r.k, q.r.eta))) break;
     if ((rc = qams_assemble(c, st))) break;
     const size_t vb = sizeof(double) * 2 * (size_t)c->N * R;
-    if (cudaMalloc(&rhs, vb) != cudaSuccess || cudaMalloc(&mu, vb) != cudaSuccess) { rc = QAMS_ECUDA; break; }
+    if ((rc = qams_dev_alloc(c, &b_rhs, vb)) || (rc = qams_dev_alloc(c, &b_mu, vb))) break;
+    rhs = b_rhs.p;
+    mu = b_mu.p;
     if ((rc = qams_incident_plane(c, R, q.dirs.data(), rhs, st))) break;
     qams_solve_opts o;
     qams_solve_opts_default(&o);
@@ -84,7 +104,8 @@ void qams_server::run(Req& q) {
     res.rel_residual = ss.rel_residual;
     if (rc) break;
     if (M > 0) {
-      if (cudaMalloc(&uinf, sizeof(double) * 2 * (size_t)M * R) != cudaSuccess) { rc = QAMS_ECUDA; break; }
+      if ((rc = qams_dev_alloc(c, &b_uinf, sizeof(double) * 2 * (size_t)M * R))) break;
+      uinf = b_uinf.p;
       if ((rc = qams_farfield(c, R, mu, M, q.far_dirs.data(), uinf, st))) break;
       if (q.r.uinf_host &&
           cudaMemcpyAsync(q.r.uinf_host, uinf, sizeof(double) * 2 * (size_t)M * R, cudaMemcpyDeviceToHost, st) !=
@@ -97,10 +118,12 @@ void qams_server::run(Req& q) {
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = QAMS_ECUDA;
   } while (false);
   if (st) cudaStreamSynchronize(st);
-  if (rhs) cudaFree(rhs);
-  if (mu) cudaFree(mu);
-  if (uinf) cudaFree(uinf);
-  if (c) qams_destroy(c);
+  if (c) {
+    qams_dev_free(c, &b_rhs);
+    qams_dev_free(c, &b_mu);
+    qams_dev_free(c, &b_uinf);
+    qams_destroy(c);  // returns every buffer to the reservation
+  }
   if (st) cudaStreamDestroy(st);
   res.status = rc;
 }
@@ -113,17 +136,21 @@ void qams_server::worker() {
       if (stop) return true;
       if (running >= slots) return false;
       for (auto& q : queue)
-        if (q->footprint + in_use <= budget) return true;
+        if (q->footprint + in_use <= budget && q->footprint <= regions.largest_free()) return true;
       return false;
     });
     if (stop) return;
-    // first queued request that fits (later small requests may pass a large one)
-    for (auto it = queue.begin(); it != queue.end(); ++it)
-      if ((*it)->footprint + in_use <= budget) {
-        pick = *it;
-        queue.erase(it);
-        break;
-      }
+    // first queued request that fits and finds a free region (later small
+    // requests may pass a large one)
+    for (auto it = queue.begin(); it != queue.end(); ++it) {
+      if ((*it)->footprint + in_use > budget) continue;
+      const long long off = regions.alloc((*it)->footprint);
+      if (off < 0) continue;
+      pick = *it;
+      pick->region = off;
+      queue.erase(it);
+      break;
+    }
     if (!pick) continue;
     in_use += pick->footprint;
     ++running;
@@ -138,6 +165,7 @@ void qams_server::worker() {
     pick->res.latency_ms = ms(pick->t_submit, pick->t_end);
     pick->res.footprint = pick->footprint;
     pick->state = 2;
+    regions.release((size_t)pick->region, pick->footprint);
     in_use -= pick->footprint;
     --running;
     cv.notify_all();
@@ -149,20 +177,27 @@ extern "C" {
 int qams_footprint(const qams_body_desc* bodies, int n_bodies, int R, int restart, size_t* bytes) {
   if (!bodies || n_bodies < 1 || R < 1 || restart < 1 || !bytes) return QAMS_EINVAL;
   size_t N = 0, blk = 0;
+  std::map<std::string, int> classes;  // congruent bodies share one block
   for (int b = 0; b < n_bodies; ++b) {
     BodyCopy bc;
     int rc = qams_copy_body(bodies[b], &bc);
     if (rc) return rc;
     const size_t n = (size_t)bodies[b].n_panels * bodies[b].order * bodies[b].n_theta;
     N += n;
-    blk += n * n;
+    if (classes.emplace(qams_shape_key(bc), b).second) blk += n * n;
   }
-  size_t f = N * (32 + 32 + 16 + 16 + 8);            // node tables
-  f += blk * (16 + 8 + 8 + 16);                       // self blocks and preconditioner
+  // an upper bound of the peak device use of one request
+  int sms = 148;
+  const long long tiles = (long long)((N + 127) / 128) + n_bodies;
+  const size_t S = (size_t)std::max(1LL, std::min<long long>(n_bodies, (8LL * sms + tiles - 1) / tiles));
+  size_t f = N * (32 + 32 + 16 + 16 + 16 + 16 + 8);   // node tables (FP64, FP32 and float-float tails, |J|)
+  f += blk * (16 + 8 + 8 + 8 + 16 + 8);               // blocks c128, c64, split copies; inverse c64, c128, split
   f += (size_t)(restart + 1) * N * R * 16;            // Krylov basis
-  f += N * R * (16 * 8 + 8 * 3);                      // solver and apply workspaces
-  f += 16 * N * (size_t)std::min(n_bodies, 64) * 16;  // pair-sum split partial sums
-  f += 64u << 20;                                     // tables, cuBLAS and rounding slack
+  f += N * R * (16 * 9 + 8 * 3);                      // solver, refinement and apply workspaces; rhs and mu
+  f += N * 4 * 64 * 2;                                // tensor-core sigma tiles (split, padded)
+  f += N * 3 * 64 * 8;                                // preconditioner panels (R, C, T of width 64)
+  f += (S > 1 ? S : 0) * N * 16 * 16;                 // pair-sum split partial sums
+  f += 64u << 20;                                     // tables, far field, alignment slack
   *bytes = f;
   return QAMS_OK;
 }
@@ -179,10 +214,15 @@ int qams_server_create(qams_server** out, int cuda_device, size_t hbm_budget, in
     QAMS_CUDA(cudaMemGetInfo(&fr, &tot));
     hbm_budget = fr - fr / 10;
   }
+  hbm_budget &= ~(size_t)255;
+  char* pool = nullptr;
+  QAMS_CUDA(cudaMalloc(&pool, hbm_budget));
   qams_server* s = new qams_server();
   s->device = cuda_device;
   s->budget = hbm_budget;
   s->slots = max_slots;
+  s->pool = pool;
+  s->regions.init(hbm_budget);
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s] { s->worker(); });
   *out = s;
   return QAMS_OK;
@@ -199,6 +239,8 @@ void qams_server_destroy(qams_server* s) {
     s->cv.notify_all();
   }
   for (auto& t : s->workers) t.join();
+  cudaSetDevice(s->device);
+  cudaFree(s->pool);
   delete s;
 }
 

@@ -11,8 +11,17 @@
 //  * QAMS_PREC_FP32: iterative refinement.  The correction equation
 //    A d = r is solved by the same GMRES with the FP32 apply (the FP64 basis
 //    vector is rounded to complex64 on the way in and the result widened on
-//    the way out) to a relative reduction inner_tol; the residual
-//    r = b - A x is recomputed with the FP64 apply after each correction.
+//    the way out) to a relative reduction inner_tol (or less, when less is
+//    enough to reach tol); the inner solve stops on its Arnoldi residual
+//    estimate.  After the first correction the residual r = b - A x is
+//    formed with the FP64-accurate apply (float-float pair sum by default),
+//    and the FP32 operator's error is measured on the same x:
+//        eta = ||(A - A_32) x|| / ||x||   (per column).
+//    A later correction d is small, and its residual is updated as
+//        r <- r - A_32 d,   error <= eta ||d||   (to first order),
+//    whenever eta ||d|| <= tol ||b|| / 2; convergence then needs
+//    ||r|| + eta ||d|| <= tol ||b||.  Otherwise r is recomputed with the
+//    FP64-accurate apply.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -107,8 +116,8 @@ __global__ void widen_kernel(const float2* __restrict__ a, double2* __restrict__
 }
 
 // r = b - y
-__global__ void residual_kernel(const double2* __restrict__ b, const double2* __restrict__ y,
-                                double2* __restrict__ r, long long n) {
+__global__ void residual_kernel(const double2* b, const double2* y,
+                                double2* r, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) r[i] = make_double2(b[i].x - y[i].x, b[i].y - y[i].y);
 }
@@ -178,6 +187,19 @@ struct Solver {
     return QAMS_OK;
   }
 
+  // y = A_32 x for FP64 x and y (no preconditioner): the FP32 operator on
+  // the rounded vector, widened
+  int apply32(const double2* x, double2* y) {
+    ++applies;
+    const long long n = N * R;
+    narrow_kernel<<<nblk(n), 256, 0, st>>>(x, (float2*)t32a.p, n); qams_count_launch();
+    int rc = qams_apply_launch(c, R, t32a.p, t32b.p, QAMS_PREC_FP32, st);
+    if (rc) return rc;
+    widen_kernel<<<nblk(n), 256, 0, st>>>((const float2*)t32b.p, y, n); qams_count_launch();
+    QAMS_CUDA(cudaGetLastError());
+    return QAMS_OK;
+  }
+
   // x <- P^{-1} x (back from the preconditioned variable), FP64
   int unprecondition(double2* x) {
     if (!prec) return QAMS_OK;
@@ -201,13 +223,21 @@ struct Solver {
     int rc = dots(v, 1, v);
     if (rc) return rc;
     out.resize(R);
-    for (int r = 0; r < R; ++r) out[r] = std::sqrt(std::max(0.0, hhost[r].x));
+    // a NaN must stay NaN (std::max(0, NaN) would return 0 and hide it)
+    for (int r = 0; r < R; ++r) {
+      const double v = hhost[r].x;
+      out[r] = std::isnan(v) ? v : std::sqrt(std::max(0.0, v));
+    }
     return QAMS_OK;
   }
 
   // GMRES for A x = b from x = 0 (x overwritten); per-column stop at
   // ||r|| <= tol * ||b||.  Returns iterations through *iters.
-  int gmres(const double2* b, double2* x, int precision, double tol, int maxit, int* iters, double* relres) {
+  //  inner = true: a correction solve inside refinement; when the Arnoldi
+  //  estimate meets tol the cycle's true residual is not recomputed (the
+  //  refinement forms its own residual next).
+  int gmres(const double2* b, double2* x, int precision, double tol, int maxit, int* iters, double* relres,
+            bool inner = false) {
     const long long n = N * R;
     QAMS_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
     std::vector<double> bn, beta;
@@ -235,6 +265,7 @@ struct Solver {
           sn((size_t)m * R);
       for (int r = 0; r < R; ++r) g[r] = beta[r];
       int j = 0;
+      bool conv = false;
       for (; j < m && it < maxit; ++j) {
         if ((rc = op(Vi(j), (double2*)w.p, precision))) return rc;
         for (int pass = 0; pass < 2; ++pass) {
@@ -279,6 +310,7 @@ struct Solver {
         ++it;
         if (all) {
           ++j;
+          conv = true;
           break;
         }
       }
@@ -298,6 +330,7 @@ struct Solver {
         QAMS_CUDA(cudaMemcpyAsync(hbuf.p, y.data(), sizeof(double2) * j * R, cudaMemcpyHostToDevice, st));
         basis_combine_kernel<<<nblk(n), 256, 0, st>>>(Vi(0), N * R, j, (const double2*)hbuf.p, x, N, R, 1.0); qams_count_launch();
       }
+      if (inner && conv) break;  // res[] holds the Arnoldi estimates
       // true residual for the restart
       if ((rc = op(x, (double2*)w.p, precision))) return rc;
       residual_kernel<<<nblk(n), 256, 0, st>>>(b, (const double2*)w.p, (double2*)w.p, n); qams_count_launch();
@@ -354,15 +387,18 @@ extern "C" int qams_solve(qams_ctx* c, int R, const void* rhs, void* mu, const q
       }
       s.refinements = 0;
     } else {
-      // iterative refinement: x = 0, r = b; repeat d = GMRES_32(r), x += d, r = b - A_64 x
-      DeviceBuf xr, rr, dd;
+      // iterative refinement: x = 0, r = b; repeat d = GMRES_32(r), x += d and
+      // a new r (FP64-accurate apply, or the residual update, see the header)
+      DeviceBuf xr, rr, dd, yy;
       rc = qams_dev_alloc(c, &xr, sizeof(double2) * n);
       if (!rc) rc = qams_dev_alloc(c, &rr, sizeof(double2) * n);
       if (!rc) rc = qams_dev_alloc(c, &dd, sizeof(double2) * n);
+      if (!rc) rc = qams_dev_alloc(c, &yy, sizeof(double2) * n);
       if (!rc) {
         cudaMemsetAsync(xr.p, 0, sizeof(double2) * n, st);
         cudaMemcpyAsync(rr.p, rhs, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st);
-        std::vector<double> bn, rn;
+        std::vector<double> bn, rn, dn, xn, en;
+        std::vector<double> eta_op;  // measured FP32 operator error per column (empty: not yet)
         rc = S.norms((const double2*)rhs, bn);
         int total = 0;
         double rel = 1.0;
@@ -370,22 +406,50 @@ extern "C" int qams_solve(qams_ctx* c, int R, const void* rhs, void* mu, const q
         for (int k = 0; !rc && k < o.max_refine; ++k) {
           int its = 0;
           double inner_rel = 0;
-          int irc = S.gmres((const double2*)rr.p, (double2*)dd.p, QAMS_PREC_FP32, o.inner_tol,
-                            std::max(1, o.max_iters - total), &its, &inner_rel);
+          // a reduction of tol/rel is enough for this correction (0.3: margin)
+          const double want = k == 0 ? o.inner_tol : std::max(o.inner_tol, std::min(0.1, 0.3 * o.tol / rel));
+          int irc = S.gmres((const double2*)rr.p, (double2*)dd.p, QAMS_PREC_FP32, want,
+                            std::max(1, o.max_iters - total), &its, &inner_rel, true);
           total += its;
           if (irc && irc != QAMS_ENOCONV) { rc = irc; break; }
           if ((rc = S.unprecondition((double2*)dd.p))) break;
           add_kernel<<<nblk(n), 256, 0, st>>>((double2*)xr.p, (const double2*)dd.p, n); qams_count_launch();
-          rc = qams_apply_launch(c, R, xr.p, dd.p, o.residual, st);
-          ++fp64_applies;
-          if (rc) break;
-          residual_kernel<<<nblk(n), 256, 0, st>>>((const double2*)rhs, (const double2*)dd.p, (double2*)rr.p, n); qams_count_launch();
-          rc = S.norms((const double2*)rr.p, rn);
-          if (rc) break;
-          rel = 0;
-          for (int r = 0; r < R; ++r) {
-            if (!std::isfinite(rn[r])) { rc = QAMS_ENUMERIC; break; }
-            rel = std::max(rel, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
+          bool update = false;
+          if (!eta_op.empty()) {
+            if ((rc = S.norms((const double2*)dd.p, dn))) break;
+            update = true;
+            for (int r = 0; r < R; ++r) update = update && eta_op[r] * dn[r] <= 0.5 * o.tol * bn[r];
+          }
+          if (update) {
+            // r <- r - A_32 d
+            if ((rc = S.apply32((const double2*)dd.p, (double2*)yy.p))) break;
+            residual_kernel<<<nblk(n), 256, 0, st>>>((const double2*)rr.p, (const double2*)yy.p, (double2*)rr.p, n); qams_count_launch();
+            if ((rc = S.norms((const double2*)rr.p, rn))) break;
+            rel = 0;
+            for (int r = 0; r < R; ++r) {
+              if (!std::isfinite(rn[r])) { rc = QAMS_ENUMERIC; break; }
+              rel = std::max(rel, bn[r] > 0 ? (rn[r] + eta_op[r] * dn[r]) / bn[r] : 0.0);
+            }
+          } else {
+            rc = qams_apply_launch(c, R, xr.p, yy.p, o.residual, st);
+            ++fp64_applies;
+            if (rc) break;
+            residual_kernel<<<nblk(n), 256, 0, st>>>((const double2*)rhs, (const double2*)yy.p, (double2*)rr.p, n); qams_count_launch();
+            if ((rc = S.norms((const double2*)rr.p, rn))) break;
+            rel = 0;
+            for (int r = 0; r < R; ++r) {
+              if (!std::isfinite(rn[r])) { rc = QAMS_ENUMERIC; break; }
+              rel = std::max(rel, bn[r] > 0 ? rn[r] / bn[r] : 0.0);
+            }
+            if (!rc && eta_op.empty() && rel > o.tol) {
+              // eta = ||A x - A_32 x|| / ||x||, dd reused for A_32 x
+              if ((rc = S.apply32((const double2*)xr.p, (double2*)dd.p))) break;
+              residual_kernel<<<nblk(n), 256, 0, st>>>((const double2*)yy.p, (const double2*)dd.p, (double2*)dd.p, n); qams_count_launch();
+              if ((rc = S.norms((const double2*)dd.p, en))) break;
+              if ((rc = S.norms((const double2*)xr.p, xn))) break;
+              eta_op.assign(R, 0.0);
+              for (int r = 0; r < R; ++r) eta_op[r] = xn[r] > 0 ? en[r] / xn[r] : 0.0;
+            }
           }
           s.refinements = k + 1;
           if (rc || rel <= o.tol || total >= o.max_iters) break;
@@ -397,6 +461,7 @@ extern "C" int qams_solve(qams_ctx* c, int R, const void* rhs, void* mu, const q
         if (!rc || rc == QAMS_ENOCONV)
           cudaMemcpyAsync(mu, xr.p, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st);
       }
+      qams_dev_free(c, &yy);
       qams_dev_free(c, &xr);
       qams_dev_free(c, &rr);
       qams_dev_free(c, &dd);

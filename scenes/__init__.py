@@ -199,6 +199,26 @@ def serving_request(request_id: int, max_bodies: int = 500) -> Scene:
     return Scene(f"serving request {request_id}", b, k, 1.0, fibonacci_directions(r, rng))
 
 
+def reduced(idx: int, n_copies: int) -> Scene:
+    """A few rigid copies of workload ``idx``'s first seeded body, with that
+    workload's discretisation, wavenumber and incident directions: each copy
+    gets a seeded rotation R_z R_y (Sec. 6.5) and a centre on a line, bounding
+    balls 1.0 apart.  Congruent copies share one self block, so an oracle
+    dense solve stays affordable at the full discretisation."""
+    base = config(idx)
+    b0 = base.bodies[0]
+    rng = np.random.default_rng(31380 + 77 * (idx + 1))
+    rb = b0.bound_radius()
+    bodies = []
+    for i in range(n_copies):
+        t1, t2 = rng.uniform(0.0, 2 * math.pi, size=2)
+        jitter = rng.uniform(-0.3, 0.3, size=2)
+        c = (i * (2 * rb + 1.0), float(jitter[0]), float(jitter[1]))
+        bodies.append(dataclasses.replace(b0, rotation=tuple(rot_zy(t1, t2)), center=c))
+    return Scene(f"{n_copies} copies of body 0 of workload {idx} ({base.name})", bodies, base.k, base.eta,
+                 base.directions)
+
+
 def small_scene(n_bodies: int = 3, n_panels: int = 1, order: int = 8, n_theta: int = 16,
                 k: float = 2.0, eta: float = 1.0, n_rhs: int = 1, seed: int = 7,
                 box: float = 6.0) -> Scene:

@@ -19,6 +19,6 @@ def test_reference_arm_prints_one_contract_line():
                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"]:
         assert key in rec, key
     assert rec["impl"] == "reference" and rec["value"] > 0
-    assert rec["config"]["workload"].startswith("16 quasi-axisymmetric bodies")
+    assert rec["config"]["workload"].startswith("1000 quasi-axisymmetric bodies")
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
     assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["e2e"]["d2h_bytes_per_step"] == 0

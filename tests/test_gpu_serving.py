@@ -79,3 +79,32 @@ def test_admission_by_budget_and_cancellation():
     spans = sorted((r["queue_ms"], r["queue_ms"] + r["run_ms"]) for r in done)
     for a, b in zip(spans, spans[1:]):
         assert b[0] >= a[1] - 1.0
+
+
+def test_large_request_in_the_mix_and_oracle_parity():
+    """A 446-body request (16 x 32 nodes, k = 6.7, 10 RHS) served together with
+    smaller ones: every result is the same alone and in the mix, and request
+    12 (10 bodies, k = 2.3, 6 RHS) matches the FP64 oracle's dense solve
+    (tests/golden/oracle_solves_serve12.npz) to the mixed-precision tolerance."""
+    import os
+
+    import paper_2606_31380_b300 as q
+    ids = [51, 12, 3, 6]
+    reqs = [scenes.serving_request(i) if i == 51 else scenes.serving_request(i, max_bodies=10) for i in ids]
+    assert len(reqs[0].bodies) == 446
+    ref = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_solves_serve12.npz"))
+    far = ref["far_dirs"]
+    srv = q.Server(0, 0, slots=1)
+    alone = [srv.wait(srv.submit(r, far)) for r in reqs]
+    srv.close()
+    srv = q.Server(0, 0, slots=4)
+    tickets = [srv.submit(r, far) for r in reqs]
+    mix = [srv.wait(t) for t in tickets]
+    srv.close()
+    for a, m in zip(alone, mix):
+        assert a["status"] == 0 and m["status"] == 0
+        assert np.max(np.abs(a["mu"] - m["mu"])) <= TOL_SAME * np.max(np.abs(a["mu"]))
+        assert np.max(np.abs(a["uinf"] - m["uinf"])) <= TOL_SAME * np.max(np.abs(a["uinf"]))
+    m12 = mix[1]
+    assert np.linalg.norm(m12["mu"] - ref["mu"]) / np.linalg.norm(ref["mu"]) < 1e-8
+    assert np.linalg.norm(m12["uinf"] - ref["uinf"]) / np.linalg.norm(ref["uinf"]) < 1e-8

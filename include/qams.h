@@ -138,21 +138,24 @@ int qams_profile_read(qams_ctx* ctx, int slot, long long* launches, double* tota
  *                        the tensor cores when R >= value (default 8;
  *                        17 = never).
  *   QAMS_OPT_TC_PAIR_MIN_RHS  the FP32 pair sum accumulates on the tensor
- *                        cores when R >= value (default 2; 17 = never).
+ *                        cores when R >= value (default 8; 17 = never).
+ *   QAMS_OPT_PAIR_TARGETS  targets per thread of the CUDA-core FP32 pair sum,
+ *                        1 (default) or 2 (each staged source serves two).
  * Errors: QAMS_EINVAL (NULL context or pointer, unknown key, value out of
  * range). */
-enum { QAMS_OPT_TC_MIN_RHS = 0, QAMS_OPT_TC_PAIR_MIN_RHS = 1 };
+enum { QAMS_OPT_TC_MIN_RHS = 0, QAMS_OPT_TC_PAIR_MIN_RHS = 1, QAMS_OPT_PAIR_TARGETS = 2 };
 int qams_set_option(qams_ctx* ctx, int key, long long value);
 int qams_get_option(const qams_ctx* ctx, int key, long long* value);
 
 /* Launch-shape autotuner (no counterpart in the paper; every candidate
  * computes the same sums up to rounding).  For R (1..16) right-hand sides on
  * the context's bodies it times, with CUDA events on `stream`, the FP32 pair
- * sum with its multiply-accumulate on the CUDA cores or on the tensor cores
- * for each distinct source-split count (about 1, 2, 4, 8 and 16 CTAs per SM),
- * and, after qams_assemble and for R >= 8, the FP32 self-block product on
- * the CUDA cores or on the tensor cores.  The fastest choices are installed in the context
- * (split tables; QAMS_OPT_TC_PAIR_MIN_RHS and QAMS_OPT_TC_MIN_RHS set so
+ * sum with its multiply-accumulate on the CUDA cores (one or two targets per
+ * thread) or on the tensor cores, for each distinct source-split count
+ * (about 1, 2, 4, 8 and 16 CTAs per SM), and, after qams_assemble and for
+ * R >= 8, the FP32 self-block product on the CUDA cores or on the tensor
+ * cores.  The fastest choices are installed in the context (split tables;
+ * QAMS_OPT_PAIR_TARGETS, QAMS_OPT_TC_PAIR_MIN_RHS and QAMS_OPT_TC_MIN_RHS set so
  * that R takes them) and cached for the process under (device, body sizes,
  * R): a later call for the same shape installs the cached choice without
  * timing (cached = 1).  Needs the bodies and the wavenumber.  Blocking.
@@ -161,6 +164,7 @@ int qams_get_option(const qams_ctx* ctx, int key, long long* value);
 typedef struct {
   int R;
   int pair_tc;      /* 1: pair sum on the tensor cores */
+  int pair_targets; /* CUDA-core pair sum: targets per thread (1 or 2) */
   int pair_splits;  /* source splits (grid rows) of the pair sum */
   int block_tc;     /* 1: block products on the tensor cores; -1: not timed (no assembly) */
   double pair_ms;   /* device time of one FP32 pair sum with the choice */
@@ -168,6 +172,16 @@ typedef struct {
   int cached;       /* 1: taken from the process-wide cache */
 } qams_tuning;
 int qams_autotune(qams_ctx* ctx, int R, qams_tuning* out, void* stream);
+
+/* Self-test of the bounded device waits (no counterpart in the paper).  The
+ * tensor-core kernels wait on mbarriers with a bound of about 2^31 clock
+ * cycles; a wait that gives up sets an error flag, the kernel drains what it
+ * issued and returns, and the call reports QAMS_ETIMEOUT.  This call
+ * launches one CTA that waits in the same way, for at most `cycles` (1 ..
+ * 2^32) clock cycles, on an mbarrier that nothing completes: it returns
+ * QAMS_ETIMEOUT (the expected result) and the device stays usable.
+ * Blocking.  Errors: QAMS_EINVAL, QAMS_ECUDA. */
+int qams_selftest_timeout(int cuda_device, long long cycles, void* stream);
 
 /* Create a context on CUDA device `cuda_device`.  hbm_budget_bytes = 0 means
  * no limit.  Errors: QAMS_EINVAL, QAMS_ECUDA. */

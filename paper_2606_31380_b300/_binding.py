@@ -16,7 +16,7 @@ PREC_FF = 2  # float-float pair sum on complex128 data
 # launch-timing slots (qams_profile_read)
 PROF_PAIRSUM_FP32, PROF_PAIRSUM_FF, PROF_PAIRSUM_FP64, PROF_BLOCK_FP32, PROF_BLOCK_FP64, PROF_ASSEMBLY, \
     PROF_BLOCK_TC, PROF_PAIRSUM_TC = range(8)
-OPT_TC_MIN_RHS, OPT_TC_PAIR_MIN_RHS = 0, 1  # qams_set_option keys
+OPT_TC_MIN_RHS, OPT_TC_PAIR_MIN_RHS, OPT_PAIR_TARGETS = 0, 1, 2  # qams_set_option keys
 
 
 def lib_path() -> str:
@@ -35,7 +35,8 @@ class SolveStats(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("R", C.c_int), ("pair_tc", C.c_int), ("pair_splits", C.c_int), ("block_tc", C.c_int),
+    _fields_ = [("R", C.c_int), ("pair_tc", C.c_int), ("pair_targets", C.c_int), ("pair_splits", C.c_int),
+                ("block_tc", C.c_int),
                 ("pair_ms", C.c_double), ("block_ms", C.c_double), ("cached", C.c_int)]
 
 
@@ -108,6 +109,7 @@ def load_library():
         "qams_profile_enable": (i, [vp, i]),
         "qams_set_option": (i, [vp, i, ll]),
         "qams_autotune": (i, [vp, i, C.POINTER(Tuning), vp]),
+        "qams_selftest_timeout": (i, [i, ll, vp]),
         "qams_get_option": (i, [vp, i, C.POINTER(ll)]),
         "qams_profile_read": (i, [vp, i, C.POINTER(ll), C.POINTER(d)]),
         "qams_precond_apply": (i, [vp, i, vp, vp, i, vp]),

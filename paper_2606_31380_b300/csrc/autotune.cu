@@ -4,8 +4,9 @@
 //
 // For R right-hand sides on a context's bodies it times, with CUDA events on
 // the caller's stream (one warm-up and two timed launches each):
-//   * the FP32 pair sum with its multiply-accumulate on the CUDA cores or on
-//     the tensor cores (R <= 16), for every distinct source-split count
+//   * the FP32 pair sum with its multiply-accumulate on the CUDA cores (one
+//     or two targets per thread) or on the tensor cores (R <= 16), for every
+//     distinct source-split count
 //     S(m) = clamp(ceil(m SMs / target tiles), 1, bodies), m in {1,2,4,8,16};
 //   * for R >= 8, the FP32 self-block product on the CUDA cores or on the
 //     tensor cores (when the split copy exists).
@@ -93,6 +94,7 @@ int run_block(void* p) {
 
 void apply_tuning(qams_ctx* c, const qams_tuning& t) {
   c->tc_pair_min_r = t.pair_tc ? t.R : std::min(17, t.R + 1);
+  c->ps_tt = t.pair_targets;
   if (t.block_tc >= 0) c->tc_min_r = t.block_tc ? t.R : std::min(17, t.R + 1);
 }
 
@@ -137,16 +139,19 @@ extern "C" int qams_autotune(qams_ctx* c, int R, qams_tuning* out, void* stream)
     const int S = qams_pairsum_default_splits(c, m);
     if (std::find(cands.begin(), cands.end(), S) == cands.end()) cands.push_back(S);
   }
-  const int saved_pair = c->tc_pair_min_r, saved_blk = c->tc_min_r;
+  const int saved_pair = c->tc_pair_min_r, saved_blk = c->tc_min_r, saved_tt = c->ps_tt;
   for (int S : cands) {
     if ((rc = qams_pairsum_set_splits(c, S))) break;
-    for (int tc = 0; tc < 2 && !rc; ++tc) {
-      c->tc_pair_min_r = tc ? 1 : 17;
+    // variants: CUDA cores with 1 or 2 targets per thread, tensor cores
+    for (int v = 0; v < 3 && !rc; ++v) {
+      c->tc_pair_min_r = v == 2 ? 1 : 17;
+      c->ps_tt = v == 1 ? 2 : 1;
       float ms = 0.f;
       rc = time_ms(st, &ms, run_pair, &job);
       if (!rc && ms < best.pair_ms) {
         best.pair_ms = ms;
-        best.pair_tc = tc;
+        best.pair_tc = v == 2;
+        best.pair_targets = v == 1 ? 2 : 1;
         best.pair_splits = S;
       }
     }
@@ -173,6 +178,7 @@ extern "C" int qams_autotune(qams_ctx* c, int R, qams_tuning* out, void* stream)
   }
   c->tc_pair_min_r = saved_pair;
   c->tc_min_r = saved_blk;
+  c->ps_tt = saved_tt;
   if (!rc) rc = qams_tc_check(c, st);
   if (!rc) rc = qams_pairsum_set_splits(c, best.pair_splits);
   qams_dev_free(c, &x);

@@ -136,7 +136,7 @@ qams_ctx::~qams_ctx() {
   prof_drain(this);
   for (DeviceBuf* b : {&x64, &n64, &x32, &n32, &x32lo, &n32lo, &centers, &boff, &jac64, &d_tiles, &d_splits, &partial,
                         &blocks64, &blocks32, &blk_off, &ws_sigma, &ws_y, &pinv32, &pinv64, &tc_blk_hi, &tc_blk_lo,
-                        &tc_pinv_hi, &tc_pinv_lo, &tc_bt, &tc_amax, &tc_err})
+                        &tc_pinv_hi, &tc_pinv_lo, &tc_bt, &tc_amax, &tc_err, &d_tiles2})
     qams_dev_free(this, b);
 }
 
@@ -155,6 +155,10 @@ int qams_set_option(qams_ctx* c, int key, long long value) {
       if (value < 1 || value > 17) return QAMS_EINVAL;
       c->tc_pair_min_r = (int)value;
       return QAMS_OK;
+    case QAMS_OPT_PAIR_TARGETS:
+      if (value != 1 && value != 2) return QAMS_EINVAL;
+      c->ps_tt = (int)value;
+      return QAMS_OK;
     default: return QAMS_EINVAL;
   }
 }
@@ -164,6 +168,7 @@ int qams_get_option(const qams_ctx* c, int key, long long* value) {
   switch (key) {
     case QAMS_OPT_TC_MIN_RHS: *value = c->tc_min_r; return QAMS_OK;
     case QAMS_OPT_TC_PAIR_MIN_RHS: *value = c->tc_pair_min_r; return QAMS_OK;
+    case QAMS_OPT_PAIR_TARGETS: *value = c->ps_tt; return QAMS_OK;
     default: return QAMS_EINVAL;
   }
 }

@@ -29,7 +29,9 @@ constexpr float INV_2PI = 0.15915494309189535f;
 constexpr float TWO_PI_HI = 6.28318548202514648f;    // float(2 pi)
 constexpr float TWO_PI_LO = -1.7484555314695172e-7f;  // 2 pi - TWO_PI_HI
 
-template <int RC>
+// TT targets per thread (tile of TT x TILE targets): each source read from
+// shared memory serves TT independent pair evaluations.
+template <int RC, int TT>
 __global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
     const TargetTile* __restrict__ tiles, const SourceSplit* __restrict__ splits,
     const long long* __restrict__ boff, const qd4* __restrict__ centers,
@@ -45,14 +47,22 @@ __global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
   const TargetTile tile = tiles[blockIdx.x];
   const SourceSplit split = splits[blockIdx.y];
   const int tid = threadIdx.x;
-  const bool active = tid < tile.count;
-  const long long t = tile.start + (active ? tid : 0);
-  const float4 xt = x32[t];
+  bool active[TT];
+  long long t[TT];
+  float4 xt[TT];
+#pragma unroll
+  for (int u = 0; u < TT; ++u) {
+    active[u] = tid + u * TILE < tile.count;
+    t[u] = tile.start + (active[u] ? tid + u * TILE : 0);
+    xt[u] = x32[t[u]];
+  }
   const float kf = (float)k, etaf = (float)eta;
 
-  float2 tot[RC];
+  float2 tot[TT][RC];
 #pragma unroll
-  for (int r = 0; r < RC; ++r) tot[r] = make_float2(0.f, 0.f);
+  for (int u = 0; u < TT; ++u)
+#pragma unroll
+    for (int r = 0; r < RC; ++r) tot[u][r] = make_float2(0.f, 0.f);
 
   for (int bb = split.begin; bb < split.end; bb += BODY_BATCH) {
     // the tile's targets share one body: its FP64 body-pair constants are
@@ -74,11 +84,15 @@ __global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
     const float fx = dcv.x, fy = dcv.y, fz = dcv.z;
     const float rho0f = dcv.w;
     const float r02 = phv.x;
-    const float At = fx * xt.x + fy * xt.y + fz * xt.z;
-
-    float2 acc[RC];
+    float At[TT];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int u = 0; u < TT; ++u) At[u] = fx * xt[u].x + fy * xt[u].y + fz * xt[u].z;
+
+    float2 acc[TT][RC];
+#pragma unroll
+    for (int u = 0; u < TT; ++u)
+#pragma unroll
+      for (int r = 0; r < RC; ++r) acc[u][r] = make_float2(0.f, 0.f);
 
     const long long send = boff[b + 1];
     for (long long s0 = boff[b]; s0 < send; s0 += CHUNK) {
@@ -96,49 +110,56 @@ __global__ void __launch_bounds__(TILE) pairsum_f32_kernel(
       }
       __syncthreads();
       const int cnt = (int)min((long long)CHUNK, send - s0);
-#pragma unroll 4
+#pragma unroll (TT == 1 ? 4 : 2)
       for (int j = 0; j < cnt; ++j) {
         const float4 p = sp[j];
         const float4 q = sq[j];
-        const float dx = xt.x - p.x, dy = xt.y - p.y, dz = xt.z - p.z;
-        const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float e = fmaf(2.f, At - p.w, dd);
-        const float r2 = r02 + e;
-        const float rinv = rsqrtf(r2);
-        const float rho = r2 * rinv;
-        const float delta = __fdividef(e, rho + rho0f);
-        const float ph = kf * delta;
-        const float nq = rintf(ph * INV_2PI);
-        float red = fmaf(-nq, TWO_PI_HI, ph);
-        red = fmaf(-nq, TWO_PI_LO, red);
-        float sn, cs;
-        __sincosf(red, &sn, &cs);
-        const float nyx = -(q.w + fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz)));
-        const float are = -nyx * rinv * rinv;
-        const float aim = fmaf(kf * nyx, rinv, -etaf);
-        const float kre = (cs * are - sn * aim) * rinv;
-        const float kim = (sn * are + cs * aim) * rinv;
 #pragma unroll
-        for (int r = 0; r < RC; ++r) {
-          const float2 s = ss[j][r];
-          acc[r].x = fmaf(kre, s.x, fmaf(-kim, s.y, acc[r].x));
-          acc[r].y = fmaf(kre, s.y, fmaf(kim, s.x, acc[r].y));
+        for (int u = 0; u < TT; ++u) {
+          const float dx = xt[u].x - p.x, dy = xt[u].y - p.y, dz = xt[u].z - p.z;
+          const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const float e = fmaf(2.f, At[u] - p.w, dd);
+          const float r2 = r02 + e;
+          const float rinv = rsqrtf(r2);
+          const float rho = r2 * rinv;
+          const float delta = __fdividef(e, rho + rho0f);
+          const float ph = kf * delta;
+          const float nq = rintf(ph * INV_2PI);
+          float red = fmaf(-nq, TWO_PI_HI, ph);
+          red = fmaf(-nq, TWO_PI_LO, red);
+          float sn, cs;
+          __sincosf(red, &sn, &cs);
+          const float nyx = -(q.w + fmaf(q.x, dx, fmaf(q.y, dy, q.z * dz)));
+          const float are = -nyx * rinv * rinv;
+          const float aim = fmaf(kf * nyx, rinv, -etaf);
+          const float kre = (cs * are - sn * aim) * rinv;
+          const float kim = (sn * are + cs * aim) * rinv;
+#pragma unroll
+          for (int r = 0; r < RC; ++r) {
+            const float2 sg = ss[j][r];
+            acc[u][r].x = fmaf(kre, sg.x, fmaf(-kim, sg.y, acc[u][r].x));
+            acc[u][r].y = fmaf(kre, sg.y, fmaf(kim, sg.x, acc[u][r].y));
+          }
         }
       }
     }
     const float c0 = phv.y, s0f = phv.z;
 #pragma unroll
-    for (int r = 0; r < RC; ++r) {
-      tot[r].x += c0 * acc[r].x - s0f * acc[r].y;
-      tot[r].y += c0 * acc[r].y + s0f * acc[r].x;
-    }
-  }
-  }
-  if (active) {
-    const float inv4pi = 0.079577471545947668f;
-    float2* o = out + split_stride * blockIdx.y + t * out_ld + out_r0;
+    for (int u = 0; u < TT; ++u)
 #pragma unroll
-    for (int r = 0; r < RC; ++r) o[r] = make_float2(tot[r].x * inv4pi, tot[r].y * inv4pi);
+      for (int r = 0; r < RC; ++r) {
+        tot[u][r].x += c0 * acc[u][r].x - s0f * acc[u][r].y;
+        tot[u][r].y += c0 * acc[u][r].y + s0f * acc[u][r].x;
+      }
+  }
+  }
+  const float inv4pi = 0.079577471545947668f;
+#pragma unroll
+  for (int u = 0; u < TT; ++u) {
+    if (!active[u]) continue;
+    float2* o = out + split_stride * blockIdx.y + t[u] * out_ld + out_r0;
+#pragma unroll
+    for (int r = 0; r < RC; ++r) o[r] = make_float2(tot[u][r].x * inv4pi, tot[u][r].y * inv4pi);
   }
 }
 
@@ -384,10 +405,19 @@ int pick_rc(int left) {
 template <int RC>
 void launch_f32(qams_ctx* c, dim3 grid, const float2* sigma, int R, int r0, float2* out, long long stride,
                 int ld, int or0, cudaStream_t st) {
-  pairsum_f32_kernel<RC><<<grid, TILE, 0, st>>>(
-      (const TargetTile*)c->d_tiles.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
-      (const qd4*)c->centers.p, (const float4*)c->x32.p, (const float4*)c->n32.p, sigma, R, r0, c->k,
-      c->eta, out, stride, ld, or0); qams_count_launch();
+  if (c->ps_tt == 2) {
+    grid.x = (unsigned)c->tiles2.size();
+    pairsum_f32_kernel<RC, 2><<<grid, TILE, 0, st>>>(
+        (const TargetTile*)c->d_tiles2.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
+        (const qd4*)c->centers.p, (const float4*)c->x32.p, (const float4*)c->n32.p, sigma, R, r0, c->k,
+        c->eta, out, stride, ld, or0);
+  } else {
+    pairsum_f32_kernel<RC, 1><<<grid, TILE, 0, st>>>(
+        (const TargetTile*)c->d_tiles.p, (const SourceSplit*)c->d_splits.p, (const long long*)c->boff.p,
+        (const qd4*)c->centers.p, (const float4*)c->x32.p, (const float4*)c->n32.p, sigma, R, r0, c->k,
+        c->eta, out, stride, ld, or0);
+  }
+  qams_count_launch();
 }
 
 template <int RC>
@@ -416,10 +446,20 @@ int qams_pairsum_prepare(qams_ctx* c) {
     const BodyHost& bh = c->bodies[b];
     for (int s = 0; s < bh.n; s += TILE) c->tiles.push_back({b, std::min(TILE, bh.n - s), bh.offset + s});
   }
+  // tiles of two targets per thread (2 TILE nodes of one body)
+  c->tiles2.clear();
+  for (int b = 0; b < (int)c->bodies.size(); ++b) {
+    const BodyHost& bh = c->bodies[b];
+    for (int s = 0; s < bh.n; s += 2 * TILE) c->tiles2.push_back({b, std::min(2 * TILE, bh.n - s), bh.offset + s});
+  }
   qams_dev_free(c, &c->d_tiles);
+  qams_dev_free(c, &c->d_tiles2);
   int rc = qams_dev_alloc(c, &c->d_tiles, sizeof(TargetTile) * c->tiles.size());
   if (rc) return rc;
+  if ((rc = qams_dev_alloc(c, &c->d_tiles2, sizeof(TargetTile) * c->tiles2.size()))) return rc;
   QAMS_CUDA(cudaMemcpy(c->d_tiles.p, c->tiles.data(), sizeof(TargetTile) * c->tiles.size(),
+                       cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(c->d_tiles2.p, c->tiles2.data(), sizeof(TargetTile) * c->tiles2.size(),
                        cudaMemcpyHostToDevice));
   return qams_pairsum_set_splits(c, qams_pairsum_default_splits(c, 8));
 }
@@ -660,7 +700,7 @@ extern "C" int qams_pairsum_f32_static(int n_bodies, const long long* body_offse
     const int ld = Sr > 1 ? rcur : R, or0 = Sr > 1 ? 0 : r0;
     const float2* sg = (const float2*)sigma_dev;
 #define QAMS_STATIC_LAUNCH(RCV)                                                                                  \
-  pairsum_f32_kernel<RCV><<<grid, TILE, 0, st>>>(d_tiles, d_splits, d_boff, d_cent, (const float4*)x32_dev,    \
+  pairsum_f32_kernel<RCV, 1><<<grid, TILE, 0, st>>>(d_tiles, d_splits, d_boff, d_cent, (const float4*)x32_dev, \
                                                  (const float4*)n32_dev, sg, R, r0, k, eta, out, stride, ld, or0)
     switch (rcur) {
       case 16: QAMS_STATIC_LAUNCH(16); break;

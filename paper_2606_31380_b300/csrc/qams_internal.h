@@ -165,7 +165,7 @@ struct qams_ctx {
   bool tc_blk_ok = false, tc_pinv_ok = false;
   int tc_bt_R = -1;
   int tc_min_r = 8;       // right-hand sides from which the FP32 block products use the tensor cores
-  int tc_pair_min_r = 2;  // ... and from which the FP32 pair sum accumulates on them
+  int tc_pair_min_r = 8;  // ... and from which the FP32 pair sum accumulates on them
 
   // launch timing of the hot kernels (QAMS_PROF_* slots of qams.h)
   bool prof = false;
@@ -173,6 +173,9 @@ struct qams_ctx {
 
   // pair-sum launch tables
   std::vector<TargetTile> tiles;
+  std::vector<TargetTile> tiles2;  // tiles of 2 TILE targets (two per thread)
+  DeviceBuf d_tiles2;
+  int ps_tt = 1;                   // targets per thread of the CUDA-core FP32 pair sum (1 or 2)
   std::vector<SourceSplit> splits;
   DeviceBuf d_tiles, d_splits;
   DeviceBuf partial;  // [splits][N][rc] partial sums (complex, largest precision)

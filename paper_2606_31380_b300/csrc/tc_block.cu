@@ -418,3 +418,43 @@ int qams_tc_check(qams_ctx* c, cudaStream_t st) {
   QAMS_CUDA(cudaStreamSynchronize(st));
   return e ? QAMS_ETIMEOUT : QAMS_OK;
 }
+
+namespace {
+// One CTA waits, as the tensor-core kernels do, on an mbarrier that nothing
+// completes; the bounded wait gives up after `cycles` and records it.
+__global__ void wait_selftest_kernel(int* err, long long cycles) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, err, cycles);
+}
+}  // namespace
+
+extern "C" int qams_selftest_timeout(int cuda_device, long long cycles, void* stream) {
+  if (cycles < 1 || cycles > (1LL << 32)) return QAMS_EINVAL;
+  int count = 0;
+  QAMS_CUDA(cudaGetDeviceCount(&count));
+  if (cuda_device < 0 || cuda_device >= count) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(cuda_device));
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d_err = nullptr;
+  QAMS_CUDA(cudaMalloc(&d_err, sizeof(int)));
+  int e = 0;
+  cudaError_t ce = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  if (ce == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(d_err, cycles);
+    qams_count_launch();
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  cudaFree(d_err);
+  if (ce != cudaSuccess) {
+    qams_internal_last_cuda_error(ce, "qams_selftest_timeout");
+    return QAMS_ECUDA;
+  }
+  return e ? QAMS_ETIMEOUT : QAMS_OK;
+}

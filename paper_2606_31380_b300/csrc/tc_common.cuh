@@ -30,11 +30,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase of parity `parity` to complete; false (and the error
-// flag set) after WAIT_CYCLES.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// flag set) after `limit` clock cycles.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, long long limit = WAIT_CYCLES) {
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       atomicExch(err, 1);
       return false;
     }

@@ -17,15 +17,18 @@
 // exact remainder (read as TF32 again), D = K_hi [S_hi; S_lo] + K_lo S_hi,
 // i.e. about 22 bits per product with FP32 accumulation.
 //
-// CTA: 256 threads for 128 targets -- warps w and w + 4 own the same
-// tensor-memory lanes (targets) and evaluate the first and second 8 of each
-// 16-source sub-chunk.  Each thread writes its K_hi and K_lo values (16
-// columns each) to tensor memory with tcgen05.st; the sigma' tile (2NH rows
-// x 32 FP32 = one 128-byte swizzle span) is written to shared memory in the
-// 128-byte-swizzled K-major layout.  One thread then issues 4 K steps x 2
-// MMAs with A read from tensor memory and B from shared memory, and commits
-// them to the buffer's mbarrier; A and B are double-buffered, so the next
-// sub-chunk's K evaluation overlaps the MMAs.  D (128 x 2NH FP32) stays in
+// CTA: eight K-evaluation warps for 128 targets -- warps w and w + 4 own the
+// same tensor-memory lanes (targets) and evaluate the first and second 8 of
+// each 16-source sub-chunk -- and one MMA warp.  The evaluation warps write
+// their K_hi and K_lo values (16 columns each) to tensor memory with
+// tcgen05.st and the sigma' tile (2NH rows x 32 FP32 = one 128-byte swizzle
+// span) to shared memory in the 128-byte-swizzled K-major layout, then each
+// arrives on the sub-chunk's "full" mbarrier.  The MMA warp waits for all
+// eight, issues 4 K steps x 2 MMAs with A read from tensor memory and B from
+// shared memory, and commits them to the buffer's "empty" mbarrier.  A and B
+// are double-buffered, so the evaluation warps run up to two sub-chunks
+// ahead of the MMAs; only body batches and 128-source staging steps
+// synchronise the CTA.  D (128 x 2NH FP32) stays in
 // tensor memory.  Accumulated in one D over all 511,488 sources of the
 // 1000-body workload, the sums came out ~2e-3 too small in magnitude -- the
 // signature of an accumulation that truncates each addition; so D is
@@ -42,7 +45,8 @@
 namespace {
 
 constexpr int TPT = 128;  // targets per CTA (MMA M)
-constexpr int NTH = 256;  // two threads per target
+constexpr int NCW = 8;               // K-evaluation warps: two threads per target
+constexpr int NTH = (NCW + 1) * 32;  // plus one warp that issues the MMAs
 constexpr int SRC = 128;  // sources staged in shared memory at a time
 constexpr int SUB = 16;   // sources per sub-chunk (K = 32 TF32 values)
 constexpr int BB = 32;    // source bodies whose body-pair constants are formed together
@@ -83,7 +87,8 @@ __global__ void __launch_bounds__(NTH, 2) pairsum_tc_kernel(TcPairArgs a) {
   __shared__ float4 sq[SRC];
   __shared__ float4 bdc[BB];  // dc = c_a - c_b (x, y, z), rho0
   __shared__ float4 bph[BB];  // rho0^2, cos k rho0, sin k rho0
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t afull[2];   // a sub-chunk's K and sigma' are in place (one arrival per evaluation warp)
+  __shared__ uint64_t aempty[2];  // its MMAs completed (tcgen05.commit)
   __shared__ uint64_t done;
   __shared__ uint32_t tslot;
   extern __shared__ uint8_t dsm[];
@@ -93,9 +98,10 @@ __global__ void __launch_bounds__(NTH, 2) pairsum_tc_kernel(TcPairArgs a) {
   const TargetTile tile = a.tiles[blockIdx.x];
   const SourceSplit split = a.splits[blockIdx.y];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool issuer = warp == NCW;         // the MMA warp
   const int row = (warp & 3) * 32 + lane;  // target within the tile = tensor-memory lane
-  const int half = warp >> 2;              // which 8 sources of a sub-chunk
-  const bool active = row < tile.count;
+  const int half = (warp >> 2) & 1;        // which 8 sources of a sub-chunk
+  const bool active = !issuer && row < tile.count;
   const long long t = tile.start + (active ? row : 0);
   const float4 xt = a.x32[t];
   const float kf = (float)a.k, etaf = (float)a.eta;
@@ -103,33 +109,40 @@ __global__ void __launch_bounds__(NTH, 2) pairsum_tc_kernel(TcPairArgs a) {
 
   for (int i = tid; i < 2 * BT / 4; i += NTH) ((float*)btile)[i] = 0.f;  // rows beyond 2R stay zero
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&afull[i], NCW);
+      mbar_init(&aempty[i], 1);
+    }
     mbar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tslot, TMEM_COLS);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeroed tiles, for the tensor cores
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tslot;
   const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
-  int g = 0;          // sub-chunks issued
-  bool bad = false;   // a bounded wait gave up
-  float acc[NH];      // warps 0-3: y columns (re R, im R) summed over finished D blocks
+  int g = 0;         // sub-chunks so far
+  bool bad = false;  // a bounded wait gave up
+  float acc[NH];     // warps 0-3: y columns (re R, im R) summed over finished D blocks
 #pragma unroll
   for (int c = 0; c < NH; ++c) acc[c] = 0.f;
   // add D block `blk` (both its parts) to acc; warps 0-3 only, after its MMAs completed
   auto fold = [&](int blk) {
-    float d[2 * NH];
     const uint32_t base = lane_base + 64 * (blk & 1);
 #pragma unroll
-    for (int c = 0; c < 2 * NH; c += 16) ld16(base + c, d + c);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int c = 0; c < NH; c += 16) {  // 16 columns of each part at a time (register pressure)
+      float d0[16], d1[16];
+      ld16(base + c, d0);
+      ld16(base + NH + c, d1);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int c = 0; c < NH; ++c) acc[c] += d[c] + d[NH + c];
+      for (int i = 0; i < 16; ++i) acc[c + i] += d0[i] + d1[i];
+    }
   };
+
   for (int bb = split.begin; bb < split.end; bb += BB) {
     __syncthreads();
     if (tid < BB && bb + tid < split.end) {
@@ -149,7 +162,33 @@ __global__ void __launch_bounds__(NTH, 2) pairsum_tc_kernel(TcPairArgs a) {
       const float At = fx * xt.x + fy * xt.y + fz * xt.z;
       const long long send = a.boff[b + 1];
       for (long long s0 = a.boff[b]; s0 < send; s0 += SRC) {
-        __syncthreads();
+        const int cnt = (int)min((long long)SRC, send - s0);
+        if (issuer) {
+          // MMA warp: per sub-chunk, wait until the evaluation warps filled it,
+          // then 4 K steps x 2 MMAs into the current D block
+          for (int j0 = 0; j0 < cnt; j0 += SUB, ++g) {
+            const int p = g & 1;
+            if (!bad) bad = !mbar_wait(&afull[p], (g >> 1) & 1, a.err);
+            if (lane == 0) {
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              constexpr uint32_t id_full = idesc_tf32(TPT, 2 * NH), id_half = idesc_tf32(TPT, NH);
+              const uint64_t bd = sdesc_sw128(btile + p * BT);
+              const uint32_t ah = tmem + 128 + 64 * p, al = ah + 32;
+              const uint32_t dt = tmem + 64 * ((g / FLUSH) & 1);
+              const int f = g % FLUSH;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) {
+                mma_tf32_ts(dt, ah + 8 * kk, bd + 2 * kk, id_full, (f | kk) != 0);
+                mma_tf32_ts(dt + NH, al + 8 * kk, bd + 2 * kk, id_half, 1u);
+              }
+              mma_commit(&aempty[p]);
+            }
+            __syncwarp();
+          }
+          continue;
+        }
+        // evaluation warps: stage the chunk's sources (named barrier of the 8 warps)
+        asm volatile("bar.sync 1, %0;" ::"r"(NCW * 32) : "memory");
         if (tid < SRC) {
           const long long i = s0 + tid;
           if (i < send) {
@@ -161,13 +200,31 @@ __global__ void __launch_bounds__(NTH, 2) pairsum_tc_kernel(TcPairArgs a) {
             sq[tid] = q;
           }
         }
-        __syncthreads();
-        const int cnt = (int)min((long long)SRC, send - s0);
+        asm volatile("bar.sync 1, %0;" ::"r"(NCW * 32) : "memory");
         for (int j0 = 0; j0 < cnt; j0 += SUB, ++g) {
           const int p = g & 1;
-          if (g >= 2 && !bad) bad = !mbar_wait(&mbar[p], ((g - 2) >> 1) & 1, a.err);
-          // the previous D block ended with sub-chunk g - 2, whose MMAs the wait above saw complete
+          // buffers p (K in tensor memory, sigma' tile) are free once sub-chunk g-2's MMAs completed
+          if (g >= 2 && !bad) bad = !mbar_wait(&aempty[p], ((g - 2) >> 1) & 1, a.err);
+          // the previous D block ended with sub-chunk g - 2: add it to the registers
           if (g % FLUSH == 1 && g / FLUSH >= 1 && warp < 4) fold(g / FLUSH - 1);
+          // sigma' tile: thread (s, r) writes its 4 hi and 4 lo values
+          uint8_t* bt = btile + p * BT;
+          if (tid < SUB * R) {
+            const int s = tid / R, r = tid - s * R;
+            float2 v = make_float2(0.f, 0.f);
+            if (j0 + s < cnt) {
+              const float2 sg = a.sigma[(s0 + j0 + s) * R + r];
+              v = make_float2(phv.y * sg.x - phv.z * sg.y, phv.y * sg.y + phv.z * sg.x);
+            }
+            const float vals[4] = {v.x, -v.y, v.y, v.x};  // (row r: 2s, 2s+1), (row R + r: 2s, 2s+1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int rr = (q < 2 ? r : R + r), kc = 2 * s + (q & 1);
+              const float h = tf32_rn(vals[q]);
+              *(float*)(bt + sw128_off(rr, kc)) = h;
+              *(float*)(bt + sw128_off(NH + rr, kc)) = vals[q] - h;
+            }
+          }
           // K for this thread's 8 sources of the sub-chunk
           float vh[16], vl[16];
 #pragma unroll
@@ -205,50 +262,19 @@ __global__ void __launch_bounds__(NTH, 2) pairsum_tc_kernel(TcPairArgs a) {
           const uint32_t abase = lane_base + 128 + 64 * p;
           st16(abase + half * 16, vh);
           st16(abase + 32 + half * 16, vl);
-          // sigma' tile: thread (s, r) writes its 4 hi and 4 lo values
-          uint8_t* bt = btile + p * BT;
-          if (tid < SUB * R) {
-            const int s = tid / R, r = tid - s * R;
-            float2 v = make_float2(0.f, 0.f);
-            if (j0 + s < cnt) {
-              const float2 sg = a.sigma[(s0 + j0 + s) * R + r];
-              v = make_float2(phv.y * sg.x - phv.z * sg.y, phv.y * sg.y + phv.z * sg.x);
-            }
-            const float vals[4] = {v.x, -v.y, v.y, v.x};  // (row r: 2s, 2s+1), (row R + r: 2s, 2s+1)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int rr = (q < 2 ? r : R + r), kc = 2 * s + (q & 1);
-              const float h = tf32_rn(vals[q]);
-              *(float*)(bt + sw128_off(rr, kc)) = h;
-              *(float*)(bt + sw128_off(NH + rr, kc)) = vals[q] - h;
-            }
-          }
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          __syncthreads();
-          if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            constexpr uint32_t id_full = idesc_tf32(TPT, 2 * NH), id_half = idesc_tf32(TPT, NH);
-            const uint64_t bd = sdesc_sw128(bt);
-            const uint32_t ah = tmem + 128 + 64 * p, al = ah + 32;
-            const uint32_t dt = tmem + 64 * ((g / FLUSH) & 1);
-            const int f = g % FLUSH;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              mma_tf32_ts(dt, ah + 8 * kk, bd + 2 * kk, id_full, (f | kk) != 0);
-              mma_tf32_ts(dt + NH, al + 8 * kk, bd + 2 * kk, id_half, 1u);
-            }
-            mma_commit(&mbar[p]);
-          }
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&afull[p])) : "memory");
         }
       }
     }
   }
-  if (tid == 0) mma_commit(&done);  // arrives once every MMA issued above has completed
+  if (issuer && lane == 0) mma_commit(&done);  // arrives once every MMA issued above has completed
   __syncthreads();
   const bool have = g > 0;
-  if (have && !mbar_wait(&done, 0, a.err)) bad = true;
+  if (have && warp < 4 && !mbar_wait(&done, 0, a.err)) bad = true;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp < 4) {
     if (have) {

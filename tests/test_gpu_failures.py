@@ -1,7 +1,8 @@
 """Failure paths of the C ABI, injected from the host (no device fault):
 overlapping bodies (QAMS_EGEOM), an iteration limit (QAMS_ENOCONV with the
 statistics filled), a non-finite right-hand side (QAMS_ENUMERIC) and an HBM
-budget below the footprint (QAMS_EBUDGET).  Each leaves the context usable."""
+budget below the footprint (QAMS_EBUDGET), and a bounded device wait that
+runs out (QAMS_ETIMEOUT).  Each leaves the context usable."""
 import numpy as np
 import pytest
 
@@ -71,7 +72,8 @@ def test_budget_below_footprint_reports_ebudget():
     import paper_2606_31380_b300 as q
     sc = scenes.small_scene(3, 1, 8, 16, k=2.0, seed=5)
     need = q.footprint(sc.bodies, 1)
-    ctx = q.Context(0, hbm_budget=need // 20)
+    # 200 KB: the node tables fit, the self blocks (3 x 128^2 complex128 = 786 KB) do not
+    ctx = q.Context(0, hbm_budget=200_000)
     with pytest.raises(q.QamsError) as e:
         ctx.set_bodies(sc.bodies)
         ctx.set_wavenumber(sc.k, sc.eta)
@@ -83,3 +85,21 @@ def test_budget_below_footprint_reports_ebudget():
     ok.set_wavenumber(sc.k, sc.eta)
     ok.assemble()
     ok.close()
+
+
+def test_bounded_device_wait_reports_etimeout():
+    """A CTA waits, the way the tensor-core kernels do, on an mbarrier that
+    nothing completes: the wait gives up after ~2^20 cycles, the call returns
+    QAMS_ETIMEOUT, and the device keeps working."""
+    import torch
+
+    import paper_2606_31380_b300 as q
+    lib = q.load_library()
+    assert lib.qams_selftest_timeout(0, 1 << 20, None) == -6  # QAMS_ETIMEOUT
+    sc = scenes.small_scene(2, 1, 8, 16, k=2.0, seed=6)
+    ctx = make_ctx(sc)
+    x = torch.from_numpy(scenes.rhs_seeded(ctx.N, 1, 1)).cuda()
+    y = torch.empty_like(x)
+    ctx.pairsum(x, y, q.PREC_FP64)
+    assert bool(torch.isfinite(y).all())
+    ctx.close()

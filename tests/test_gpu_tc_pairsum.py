@@ -62,3 +62,26 @@ def test_tc_pairsum_thousand_bodies_sampled_rows_against_oracle():
     got = y.cpu().numpy()[rows].astype(np.complex128)
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < FP32_TOL
     ctx.close()
+
+
+@pytest.mark.parametrize("R", [1, 4, 16])
+def test_two_targets_per_thread_matches_fp64(R):
+    """The CUDA-core FP32 pair sum with two targets per thread (tiles of 256
+    targets, ragged) against the FP64 pair sum."""
+    import torch
+
+    import paper_2606_31380_b300 as q
+    sc = scenes.small_scene(5, 1, 8, 40, k=6.0, eta=1.0, seed=33, box=10.0)  # 320-node bodies
+    ctx = make_ctx(sc)
+    s64 = torch.from_numpy(scenes.rhs_seeded(ctx.N, R, 70 + R)).cuda()
+    ref = torch.empty_like(s64)
+    ctx.pairsum(s64, ref, q.PREC_FP64)
+    ctx.set_option(q.OPT_TC_PAIR_MIN_RHS, 17)
+    ctx.set_option(q.OPT_PAIR_TARGETS, 2)
+    y = torch.full_like(s64.to(torch.complex64), float("nan"))
+    ctx.pairsum(s64.to(torch.complex64), y, q.PREC_FP32)
+    r = ref.cpu().numpy()
+    a = y.cpu().numpy().astype(np.complex128)
+    assert np.all(np.isfinite(a))
+    assert np.max(np.abs(a - r)) / np.max(np.abs(r)) < FP32_TOL
+    ctx.close()

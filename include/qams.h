@@ -126,7 +126,8 @@ enum {
   QAMS_PROF_ASSEMBLY = 5,     /* self-block assembly kernel */
   QAMS_PROF_BLOCK_TC = 6,     /* self-block / preconditioner products on the tensor cores */
   QAMS_PROF_PAIRSUM_TC = 7,   /* FP32 pair sum with its accumulation on the tensor cores */
-  QAMS_PROF_COUNT = 8
+  QAMS_PROF_PAIRSUM_LATTICE = 8, /* pair sum of a lattice through the circulant embedding (all passes) */
+  QAMS_PROF_COUNT = 9
 };
 int qams_profile_enable(qams_ctx* ctx, int on);
 int qams_profile_read(qams_ctx* ctx, int slot, long long* launches, double* total_ms);
@@ -141,9 +142,18 @@ int qams_profile_read(qams_ctx* ctx, int slot, long long* launches, double* tota
  *                        cores when R >= value (default 8; 17 = never).
  *   QAMS_OPT_PAIR_TARGETS  targets per thread of the CUDA-core FP32 pair sum,
  *                        1 (default) or 2 (each staged source serves two).
+ *   QAMS_OPT_NEAR_FIELD  qams_field's near-field correction for points within
+ *                        value node spacings of a body (0 = smooth rule
+ *                        only; 1..64; default 6).
+ *   QAMS_OPT_LATTICE     on a context set by qams_set_lattice: 1 (default)
+ *                        applies the pair sum through the circulant
+ *                        embedding once qams_lattice_prepare (or
+ *                        qams_assemble) has built it; 0 = the direct pair
+ *                        sum over all node pairs.
  * Errors: QAMS_EINVAL (NULL context or pointer, unknown key, value out of
  * range). */
-enum { QAMS_OPT_TC_MIN_RHS = 0, QAMS_OPT_TC_PAIR_MIN_RHS = 1, QAMS_OPT_PAIR_TARGETS = 2 };
+enum { QAMS_OPT_TC_MIN_RHS = 0, QAMS_OPT_TC_PAIR_MIN_RHS = 1, QAMS_OPT_PAIR_TARGETS = 2, QAMS_OPT_LATTICE = 3,
+       QAMS_OPT_NEAR_FIELD = 4 };
 int qams_set_option(qams_ctx* ctx, int key, long long value);
 int qams_get_option(const qams_ctx* ctx, int key, long long* value);
 
@@ -195,6 +205,37 @@ void qams_destroy(qams_ctx* ctx);
  * Errors: QAMS_EINVAL (n_bodies < 1, n_theta odd or < 2, order < 1,
  * n_panels < 1, n_modes > 8), QAMS_EGEOM, QAMS_EBUDGET, QAMS_ECUDA. */
 int qams_set_bodies(qams_ctx* ctx, int n_bodies, const qams_body_desc* bodies, double min_gap);
+
+/* A regular lattice of one rigid shape (Sec. 4, regular P x Q x R arrays
+ * with uniform spacing; Table tab:multibody_cubic).  Sets the context's
+ * bodies to dims[0] dims[1] dims[2] copies of *body (same reference shape,
+ * same rotation) with centres body->center + p a0 + q a1 + r a2, where a0,
+ * a1, a2 are the rows of basis (row-major 3x3, host) and body index
+ * (p dims[1] + q) dims[2] + r, so node order is p, q, r, then the body's own
+ * order.  The inter-body block of bodies t and s then depends only on
+ * their displacement d = (p_t - p_s, q_t - q_s, r_t - r_s) (the block
+ * Toeplitz structure of Sec. 4).  qams_lattice_prepare (called by
+ * qams_assemble) forms the (2 dims[0] - 1)(2 dims[1] - 1)(2 dims[2] - 1)
+ * distinct blocks T(d)[i][j] = K(x~_i + d.A, y~_j) in FP64, embeds them in
+ * a circulant of those periods and transforms them by the 3-D discrete
+ * Fourier transform; from then on qams_pairsum (and so qams_apply and
+ * qams_solve) computes the same sums as the direct pair sum by per-frequency
+ * n x n products: complex64 blocks for QAMS_PREC_FP32, complex128 for
+ * QAMS_PREC_FF and QAMS_PREC_FP64 (FP64 throughout; no phase split is
+ * needed).  Library-owned device memory: (16 + 8) n^2 prod(2 dims - 1)
+ * bytes of blocks plus two [prod(2 dims - 1)][n][R] complex workspaces
+ * sized at the first apply.  A later qams_set_bodies ends the lattice mode.
+ * Checks and errors as qams_set_bodies; QAMS_EINVAL also for dims outside
+ * 1..32 or a non-finite basis.  Blocking. */
+int qams_set_lattice(qams_ctx* ctx, const qams_body_desc* body, const int dims_host[3], const double basis_host[9],
+                     double min_gap);
+
+/* Build the transformed displacement blocks of a lattice context for the
+ * current wavenumber (see qams_set_lattice); qams_assemble calls it when
+ * QAMS_OPT_LATTICE is on.  A new wavenumber invalidates them.  Blocking.
+ * Errors: QAMS_EINVAL (not a lattice context, no wavenumber), QAMS_EBUDGET,
+ * QAMS_ECUDA. */
+int qams_lattice_prepare(qams_ctx* ctx, void* stream);
 
 /* N (total nodes) and the first node of every body (n_bodies+1 offsets). */
 int qams_node_count(const qams_ctx* ctx, long long* n_nodes);
@@ -377,13 +418,28 @@ int qams_farfield(qams_ctx* ctx, int R, const void* mu_dev, int M, const double*
 
 /* Scattered field u = (D - i eta S)[mu] at M off-surface points
  * points_host [M][3] (Sec. 6: the field compared with the point-source
- * solution), by the smooth rule on the surface nodes:
- *   u(x) = sum_y [(ik/rho - 1/rho^2) n(y).(y - x) - i eta] e^{ik rho}/(4 pi rho) w mu(y).
- * Accurate for points whose distance to every surface exceeds a few node
- * spacings; no near-singular correction is applied.  mu_dev [N][R] and
- * u_dev [M][R] are complex128.  Blocking on `stream`. */
+ * solution of Eq. artificial point source solution), by the smooth rule on
+ * the surface nodes,
+ *   u(x) = sum_y [(ik/rho - 1/rho^2) n(y).(y - x) - i eta] e^{ik rho}/(4 pi rho) w mu(y),
+ * with a near-field correction: for a point within f node spacings of a
+ * body (f = QAMS_OPT_NEAR_FIELD, default 6; the spacing is the body's
+ * largest distance between neighbouring nodes) the body's smooth-rule terms
+ * on the panels within one of the nearest point's panel are replaced by
+ * the self blocks' product integration (Sec. 3) taken at the off-surface
+ * target: modal Green's functions of the source rings seen from x, the
+ * outer integral graded toward the nearest surface point (found on the host
+ * by Gauss-Newton from the nearest node).  The result is then the layer
+ * potential of the interpolated density on those panels, accurate at any
+ * distance off the surface; points on a surface are not supported.  mu_dev
+ * [N][R] and u_dev [M][R] are complex128.  Blocking on `stream`.
+ * Errors: QAMS_EINVAL (also a near point whose ring bandwidth k (r + d)
+ * exceeds the self-block kernel's tables, as qams_assemble), QAMS_EBUDGET,
+ * QAMS_ECUDA. */
 int qams_field(qams_ctx* ctx, int R, const void* mu_dev, int M, const double* points_host, void* u_dev,
                void* stream);
+
+/* (point, body) pairs the last qams_field corrected in the near field. */
+int qams_field_near_pairs(const qams_ctx* ctx, long long* pairs);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop over independent scattering problems (the

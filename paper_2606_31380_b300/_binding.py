@@ -15,8 +15,8 @@ PREC_FP32 = 1
 PREC_FF = 2  # float-float pair sum on complex128 data
 # launch-timing slots (qams_profile_read)
 PROF_PAIRSUM_FP32, PROF_PAIRSUM_FF, PROF_PAIRSUM_FP64, PROF_BLOCK_FP32, PROF_BLOCK_FP64, PROF_ASSEMBLY, \
-    PROF_BLOCK_TC, PROF_PAIRSUM_TC = range(8)
-OPT_TC_MIN_RHS, OPT_TC_PAIR_MIN_RHS, OPT_PAIR_TARGETS = 0, 1, 2  # qams_set_option keys
+    PROF_BLOCK_TC, PROF_PAIRSUM_TC, PROF_PAIRSUM_LATTICE = range(9)
+OPT_TC_MIN_RHS, OPT_TC_PAIR_MIN_RHS, OPT_PAIR_TARGETS, OPT_LATTICE, OPT_NEAR_FIELD = 0, 1, 2, 3, 4  # option keys
 
 
 def lib_path() -> str:
@@ -113,6 +113,9 @@ def load_library():
         "qams_get_option": (i, [vp, i, C.POINTER(ll)]),
         "qams_profile_read": (i, [vp, i, C.POINTER(ll), C.POINTER(d)]),
         "qams_precond_apply": (i, [vp, i, vp, vp, i, vp]),
+        "qams_set_lattice": (i, [vp, C.POINTER(BodyDesc), vp, vp, d]),
+        "qams_lattice_prepare": (i, [vp, vp]),
+        "qams_field_near_pairs": (i, [vp, C.POINTER(ll)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -228,6 +231,23 @@ class Context:
         _check(self.lib.qams_node_count(self._h, C.byref(n)), "qams_node_count")
         self.N = int(n.value)
         self.n_bodies = len(bodies)
+
+    def set_lattice(self, body, dims, basis, min_gap: float = 0.0):
+        """dims[0] x dims[1] x dims[2] copies of ``body`` at body.center + p a0 + q a1 + r a2
+        (a_i the rows of the 3x3 ``basis``), body index (p dims[1] + q) dims[2] + r."""
+        arr, keep = body_desc_array([body])
+        d = (C.c_int * 3)(*[int(v) for v in dims])
+        bs = np.ascontiguousarray(np.asarray(basis, dtype=np.float64).reshape(9))
+        _check(self.lib.qams_set_lattice(self._h, arr, C.cast(d, C.c_void_p), bs.ctypes.data_as(C.c_void_p),
+                                         float(min_gap)), "qams_set_lattice")
+        n = C.c_longlong()
+        _check(self.lib.qams_node_count(self._h, C.byref(n)), "qams_node_count")
+        self.N = int(n.value)
+        self.n_bodies = int(dims[0]) * int(dims[1]) * int(dims[2])
+
+    def lattice_prepare(self, stream=None):
+        """Build the transformed displacement blocks of a lattice context."""
+        _check(self.lib.qams_lattice_prepare(self._h, C.c_void_p(_stream_ptr(stream))), "qams_lattice_prepare")
 
     def body_offsets(self) -> np.ndarray:
         off = np.zeros(self.n_bodies + 1, np.int64)
@@ -389,6 +409,12 @@ class Context:
                                    points.ctypes.data_as(C.c_void_p),
                                    _dev(u, torch.complex128, (M, R), "u"),
                                    C.c_void_p(_stream_ptr(stream))), "qams_field")
+
+    def field_near_pairs(self) -> int:
+        """(point, body) pairs the last field() call corrected in the near field."""
+        v = C.c_longlong()
+        _check(self.lib.qams_field_near_pairs(self._h, C.byref(v)), "qams_field_near_pairs")
+        return int(v.value)
 
 
 QAMS_EAGAIN = -10

@@ -138,6 +138,7 @@ qams_ctx::~qams_ctx() {
                         &blocks64, &blocks32, &blk_off, &ws_sigma, &ws_y, &pinv32, &pinv64, &tc_blk_hi, &tc_blk_lo,
                         &tc_pinv_hi, &tc_pinv_lo, &tc_bt, &tc_amax, &tc_err, &d_tiles2})
     qams_dev_free(this, b);
+  qams_lattice_reset(this);
 }
 
 extern "C" {
@@ -159,6 +160,14 @@ int qams_set_option(qams_ctx* c, int key, long long value) {
       if (value != 1 && value != 2) return QAMS_EINVAL;
       c->ps_tt = (int)value;
       return QAMS_OK;
+    case QAMS_OPT_LATTICE:
+      if (value != 0 && value != 1) return QAMS_EINVAL;
+      c->lat.use = value != 0;
+      return QAMS_OK;
+    case QAMS_OPT_NEAR_FIELD:
+      if (value < 0 || value > 64) return QAMS_EINVAL;
+      c->near_factor = (int)value;
+      return QAMS_OK;
     default: return QAMS_EINVAL;
   }
 }
@@ -169,6 +178,8 @@ int qams_get_option(const qams_ctx* c, int key, long long* value) {
     case QAMS_OPT_TC_MIN_RHS: *value = c->tc_min_r; return QAMS_OK;
     case QAMS_OPT_TC_PAIR_MIN_RHS: *value = c->tc_pair_min_r; return QAMS_OK;
     case QAMS_OPT_PAIR_TARGETS: *value = c->ps_tt; return QAMS_OK;
+    case QAMS_OPT_LATTICE: *value = c->lat.use ? 1 : 0; return QAMS_OK;
+    case QAMS_OPT_NEAR_FIELD: *value = c->near_factor; return QAMS_OK;
     default: return QAMS_EINVAL;
   }
 }
@@ -242,6 +253,7 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
       if (std::sqrt(dx * dx + dy * dy + dz * dz) < rad[i] + rad[j] + min_gap) return QAMS_EGEOM;
     }
   QAMS_CUDA(cudaSetDevice(c->device));
+  qams_lattice_reset(c);
   for (DeviceBuf* b : {&c->x64, &c->n64, &c->x32, &c->n32, &c->x32lo, &c->n32lo, &c->centers, &c->boff, &c->jac64, &c->blocks64,
                        &c->blocks32, &c->blk_off, &c->ws_sigma, &c->ws_y, &c->pinv32, &c->pinv64, &c->tc_blk_hi,
                        &c->tc_blk_lo, &c->tc_pinv_hi, &c->tc_pinv_lo, &c->tc_bt})
@@ -320,6 +332,43 @@ int qams_set_bodies(qams_ctx* c, int n_bodies, const qams_body_desc* bodies, dou
   return qams_pairsum_prepare(c);
 }
 
+int qams_set_lattice(qams_ctx* c, const qams_body_desc* body, const int* dims, const double* basis, double min_gap) {
+  if (!c || !body || !dims || !basis) return QAMS_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 1 || dims[a] > 32) return QAMS_EINVAL;
+  for (int a = 0; a < 9; ++a)
+    if (!std::isfinite(basis[a])) return QAMS_EINVAL;
+  const int nb = dims[0] * dims[1] * dims[2];
+  std::vector<qams_body_desc> d(nb, *body);
+  for (int p = 0; p < dims[0]; ++p)
+    for (int q = 0; q < dims[1]; ++q)
+      for (int r = 0; r < dims[2]; ++r) {
+        qams_body_desc& b = d[(p * dims[1] + q) * dims[2] + r];
+        for (int x = 0; x < 3; ++x) b.center[x] = body->center[x] + p * basis[x] + q * basis[3 + x] + r * basis[6 + x];
+      }
+  int rc = qams_set_bodies(c, nb, d.data(), min_gap);
+  if (rc) return rc;
+  LatticeState& L = c->lat;
+  L.on = true;
+  L.ready = false;
+  L.n = c->bodies[0].n;
+  for (int a = 0; a < 3; ++a) {
+    L.P[a] = dims[a];
+    L.L[a] = 2 * dims[a] - 1;
+  }
+  std::copy(basis, basis + 9, L.basis);
+  return QAMS_OK;
+}
+
+int qams_lattice_prepare(qams_ctx* c, void* stream) {
+  if (!c || !c->lat.on || !c->have_k) return QAMS_EINVAL;
+  QAMS_CUDA(cudaSetDevice(c->device));
+  int rc = qams_lattice_prepare_launch(c, (cudaStream_t)stream);
+  if (rc) return rc;
+  QAMS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return QAMS_OK;
+}
+
 int qams_node_count(const qams_ctx* c, long long* n) {
   if (!c || !n) return QAMS_EINVAL;
   *n = c->N;
@@ -346,6 +395,7 @@ int qams_set_wavenumber(qams_ctx* c, double k, double eta) {
   c->k = k;
   c->eta = eta;
   c->have_k = true;
+  c->lat.ready = false;
   return QAMS_OK;
 }
 
@@ -365,6 +415,7 @@ int qams_assemble(qams_ctx* c, void* stream) {
   if (rc) return rc;
   rc = qams_blocks_to_fp32(c, (cudaStream_t)stream);
   if (rc) return rc;
+  if (c->lat.on && c->lat.use && (rc = qams_lattice_prepare_launch(c, (cudaStream_t)stream))) return rc;
   c->assembled = true;
   return QAMS_OK;
 }
@@ -441,6 +492,12 @@ int qams_farfield(qams_ctx* c, int R, const void* mu, int M, const double* dirs,
   if (!c || R < 1 || M < 1 || !mu || !dirs || !uinf || c->bodies.empty() || !c->have_k) return QAMS_EINVAL;
   QAMS_CUDA(cudaSetDevice(c->device));
   return qams_farfield_launch(c, R, mu, M, dirs, uinf, (cudaStream_t)stream);
+}
+
+int qams_field_near_pairs(const qams_ctx* c, long long* pairs) {
+  if (!c || !pairs) return QAMS_EINVAL;
+  *pairs = c->near_pairs;
+  return QAMS_OK;
 }
 
 int qams_field(qams_ctx* c, int R, const void* mu, int M, const double* points, void* u, void* stream) {

@@ -245,5 +245,5 @@ int qams_field_launch(qams_ctx* c, int R, const void* mu, int M, const double* p
   }
   QAMS_CUDA(cudaStreamSynchronize(st));
   qams_dev_free(c, &d);
-  return QAMS_OK;
+  return qams_near_correction(c, R, mu, M, pts_host, u, st);
 }

@@ -266,6 +266,95 @@ extern "C" int qams_body_nodes(const qams_body_desc* desc, double* x_host, doubl
   return QAMS_OK;
 }
 
+void qams_nearest_point(const BodyHost& b, const double* hx_body, const double x[3], double* s_out,
+                        double* th_out, int* panel_out, double* dist_out, double v_out[3]) {
+  const qams_body_desc& d = b.d;
+  Shape sh{b};
+  // body-local target
+  double xl[3];
+  for (int q = 0; q < 3; ++q) {
+    xl[q] = 0.0;
+    for (int r = 0; r < 3; ++r) xl[q] += d.rotation[3 * r + q] * (x[r] - d.center[r]);
+  }
+  // start at the nearest node
+  long long best = 0;
+  double bd = 1e300;
+  for (long long t = 0; t < b.n; ++t) {
+    const double dx = hx_body[3 * t] - x[0], dy = hx_body[3 * t + 1] - x[1], dz = hx_body[3 * t + 2] - x[2];
+    const double dd = dx * dx + dy * dy + dz * dz;
+    if (dd < bd) {
+      bd = dd;
+      best = t;
+    }
+  }
+  std::vector<double> gx, gw;
+  qams_gauss_legendre(d.order, gx, gw);
+  const int per_panel = d.order * d.n_theta;
+  const int p0 = (int)(best / per_panel), l0 = (int)((best % per_panel) / d.n_theta), j0 = (int)(best % d.n_theta);
+  double s = 0.5 * (b.breaks[p0] + b.breaks[p0 + 1]) + 0.5 * (b.breaks[p0 + 1] - b.breaks[p0]) * gx[l0];
+  double th = 2.0 * M_PI * j0 / d.n_theta;
+  const double smax = 0.5 * M_PI - 1e-7;
+  // Gauss-Newton on |x - y(s, th)|^2 with difference Jacobians (their error only slows
+  // the iteration; the fixed point is set by the exact residual)
+  for (int it = 0; it < 60; ++it) {
+    double p[3], nn[3], jac, pa[3], pb[3], dummy;
+    const double hs = 1e-6, ht = 1e-6;
+    sh.eval(s, th, p, nn, &jac);
+    const double sa = std::min(smax, s + hs), sb = std::max(-smax, s - hs);
+    sh.eval(sa, th, pa, nn, &dummy);
+    sh.eval(sb, th, pb, nn, &dummy);
+    double Js[3], Jt[3];
+    for (int q = 0; q < 3; ++q) Js[q] = (pa[q] - pb[q]) / (sa - sb);
+    sh.eval(s, th + ht, pa, nn, &dummy);
+    sh.eval(s, th - ht, pb, nn, &dummy);
+    for (int q = 0; q < 3; ++q) Jt[q] = (pa[q] - pb[q]) / (2.0 * ht);
+    double r[3];
+    for (int q = 0; q < 3; ++q) r[q] = xl[q] - p[q];
+    double a11 = 0, a12 = 0, a22 = 0, g1 = 0, g2 = 0;
+    for (int q = 0; q < 3; ++q) {
+      a11 += Js[q] * Js[q];
+      a12 += Js[q] * Jt[q];
+      a22 += Jt[q] * Jt[q];
+      g1 += Js[q] * r[q];
+      g2 += Jt[q] * r[q];
+    }
+    const double lam = 1e-12 * (a11 + a22);
+    a11 += lam;
+    a22 += lam;
+    const double det = a11 * a22 - a12 * a12;
+    if (!(det > 0.0)) break;
+    double ds = (a22 * g1 - a12 * g2) / det, dt = (a11 * g2 - a12 * g1) / det;
+    // keep steps inside a node spacing's order of magnitude
+    ds = std::max(-0.25, std::min(0.25, ds));
+    dt = std::max(-0.5, std::min(0.5, dt));
+    s = std::max(-smax, std::min(smax, s + ds));
+    th += dt;
+    if (std::fabs(ds) < 1e-13 && std::fabs(dt) < 1e-13) break;
+  }
+  th = std::fmod(th, 2.0 * M_PI);
+  if (th < 0) th += 2.0 * M_PI;
+  double p[3], nn[3], jac;
+  sh.eval(s, th, p, nn, &jac);
+  double v[3];
+  for (int q = 0; q < 3; ++q) v[q] = xl[q] - p[q];
+  *dist_out = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  if (d.profile_kind == 1) {
+    for (int q = 0; q < 3; ++q) v_out[q] = v[q];
+  } else {
+    // components in (e1, e2, e3)(s) of the arc axis
+    const double kl = d.curvature * 0.5 * d.axis_length * std::sin(s);
+    const double ck = std::cos(kl), sk = std::sin(kl);
+    v_out[0] = ck * v[0] - sk * v[2];
+    v_out[1] = v[1];
+    v_out[2] = sk * v[0] + ck * v[2];
+  }
+  int pan = 0;
+  while (pan + 1 < d.n_panels && s >= b.breaks[pan + 1]) ++pan;
+  *s_out = s;
+  *th_out = th;
+  *panel_out = pan;
+}
+
 std::string qams_shape_key(const BodyCopy& bc) {
   const qams_body_desc& d = bc.d;
   std::string k;

@@ -502,6 +502,7 @@ int qams_pairsum_set_splits(qams_ctx* c, int S) {
 }
 
 int qams_pairsum_launch(qams_ctx* c, int R, const void* sigma, void* y, int precision, cudaStream_t st) {
+  if (c->lat.on && c->lat.use && c->lat.ready) return qams_lattice_pairsum(c, R, sigma, y, precision, st);
   const int S = (int)c->splits.size();
   dim3 grid((unsigned)c->tiles.size(), (unsigned)S);
   if (precision == QAMS_PREC_FP32 && R >= c->tc_pair_min_r && R <= 16) {

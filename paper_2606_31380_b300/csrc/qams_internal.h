@@ -55,6 +55,13 @@ struct BodyHost : BodyCopy {
   int n = 0;             // nodes
 };
 
+// Nearest point of body b (world nodes hx_body [n][3]) to the world point x:
+// surface parameters (s, th) and panel, distance, and v = x - y(s, th) in the
+// frame the self-block kernel takes target offsets in (arc axis: (e1, e2,
+// e3)(s); ring-series shapes: the body frame).
+void qams_nearest_point(const BodyHost& b, const double* hx_body, const double x[3], double* s, double* th,
+                        int* panel, double* dist, double v[3]);
+
 // One target tile of the pair sum: up to TILE consecutive nodes of one body.
 struct TargetTile {
   int body;
@@ -109,6 +116,22 @@ struct TcGroup {
   int first, nb, n;    // first body, bodies, nodes per body
   long long node0;     // first node of the first body
   long long elem0;     // first complex block entry of the first body
+};
+
+// A regular lattice of one rigid shape (qams_set_lattice): bodies
+// (p Q + q) R + r at c_0 + p a0 + q a1 + r a2, all with one rotation.  The
+// pair sum then runs through the circulant embedding of lattice.cu.
+struct LatticeState {
+  bool on = false;           // bodies were set by qams_set_lattice
+  bool use = true;           // QAMS_OPT_LATTICE
+  bool ready = false;        // transformed blocks built for the current wavenumber
+  int P[3] = {1, 1, 1};      // bodies along each lattice vector
+  int L[3] = {1, 1, 1};      // circulant periods 2 P - 1
+  double basis[9] = {};      // lattice vectors a0, a1, a2 (rows)
+  int n = 0;                 // nodes per body
+  DeviceBuf that64, that32;  // [L0 L1 L2][n][n] transformed displacement blocks
+  DeviceBuf tw;              // twiddle tables
+  DeviceBuf work, work2;     // [L0 L1 L2][n][R] transform workspaces
 };
 
 struct qams_ctx {
@@ -169,7 +192,7 @@ struct qams_ctx {
 
   // launch timing of the hot kernels (QAMS_PROF_* slots of qams.h)
   bool prof = false;
-  ProfSlot prof_slots[8];
+  ProfSlot prof_slots[QAMS_PROF_COUNT];
 
   // pair-sum launch tables
   std::vector<TargetTile> tiles;
@@ -179,6 +202,13 @@ struct qams_ctx {
   std::vector<SourceSplit> splits;
   DeviceBuf d_tiles, d_splits;
   DeviceBuf partial;  // [splits][N][rc] partial sums (complex, largest precision)
+
+  LatticeState lat;
+
+  // near-field correction of qams_field (QAMS_OPT_NEAR_FIELD): points closer
+  // than near_factor node spacings to a body get the product-integration rows
+  int near_factor = 6;
+  long long near_pairs = 0;  // (point, body) pairs corrected by the last qams_field
 
   ~qams_ctx();
 };
@@ -200,8 +230,26 @@ int qams_pairsum_prepare(qams_ctx* c);
 int qams_pairsum_set_splits(qams_ctx* c, int S);
 int qams_pairsum_default_splits(const qams_ctx* c, int mult);
 
+// An off-surface target near one body (the near-field rows of selfblock.cu):
+// x = y(s, th) + v with v = nu n^(s, th), the unit normal's components taken in
+// the target ring's frame (e1, e2, e3)(s) for arc-axis bodies and in the
+// body frame for ring-series bodies.
+struct NearTarget {
+  int cls;          // class of congruent bodies (index into class_rep)
+  int panel;        // panel holding s
+  double s, th;     // closest surface point
+  double v[3];      // offset nu n^
+  double x[3];      // world position (for the smooth-rule subtraction)
+  long long node0;  // first node of the body
+  long long row;    // first entry of the target's row in the output
+  int m;            // target point (row of the field output)
+  int n;            // nodes of the body (row length)
+};
+
 // selfblock.cu
 int qams_assemble_launch(qams_ctx* c, cudaStream_t st);
+int qams_near_rows_launch(qams_ctx* c, const NearTarget* targets, long long n, double r_extra, double2* rows,
+                          cudaStream_t st);
 
 // blockops.cu
 int qams_blocks_to_fp32(qams_ctx* c, cudaStream_t st);
@@ -223,9 +271,18 @@ int qams_tc_check(qams_ctx* c, cudaStream_t st);
 int qams_pairsum_tc_launch(qams_ctx* c, int R, const void* sigma, void* out, long long split_stride, int out_ld,
                            cudaStream_t st);
 
+// lattice.cu
+int qams_lattice_prepare_launch(qams_ctx* c, cudaStream_t st);
+int qams_lattice_pairsum(qams_ctx* c, int R, const void* sigma, void* y, int precision, cudaStream_t st);
+void qams_lattice_reset(qams_ctx* c);
+
 // fields.cu
 int qams_incident_launch(qams_ctx* c, int R, const double* dirs_host, void* rhs, cudaStream_t st);
 int qams_field_launch(qams_ctx* c, int R, const void* mu, int M, const double* pts_host, void* u,
                       cudaStream_t st);
+
+// nearfield.cu: adds the near-field rows' contributions to a smooth-rule field
+int qams_near_correction(qams_ctx* c, int R, const void* mu, int M, const double* pts_host, void* u,
+                         cudaStream_t st);
 int qams_farfield_launch(qams_ctx* c, int R, const void* mu, int M, const double* dirs_host, void* uinf,
                          cudaStream_t st);

@@ -200,7 +200,8 @@ __device__ __forceinline__ void series_at(const double* T, int nt, double s, dou
 }
 
 __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, double s_t, double th_t, double h,
-                          int P, int Nhalf, const double* __restrict__ inv_odd, double* q, double* dq, double* sc) {
+                          int P, int Nhalf, const double* __restrict__ inv_odd, double* q, double* dq, double* sc,
+                          const double* off) {
   const double s = s_t + h;
   const double sh = sin(0.5 * h);
   const double mid = s_t + 0.5 * h;
@@ -227,9 +228,19 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
     rt = hypot(a, b);
     const double drt = (2.0 * r_t * (ct * dx + st * dy) + dx * dx + dy * dy) / (rt + r_t);  // r~ - r_t
     dr = -drop[3] - drt;
-    alpha = atan2(b, a);
-    ca = a / rt;
-    sa = b / rt;
+    double ao = a, bo = b;
+    if (off) {
+      // off-surface target y_t + v (v = nu n^ in the body frame, which is every ring's frame here)
+      ao = a + off[0];
+      bo = b + off[1];
+      const double rto = hypot(ao, bo);
+      dr -= (2.0 * (a * off[0] + b * off[1]) + off[0] * off[0] + off[1] * off[1]) / (rto + rt);
+      rt = rto;
+      c += off[2];
+    }
+    alpha = atan2(bo, ao);
+    ca = ao / rt;
+    sa = bo / rt;
     a0 = r * df[2];
     a1 = 0.0;
     b0 = -r * df[3];
@@ -265,9 +276,22 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
     rt = hypot(a, b);
     const double d2 = -(r_t * ct * skd) * (r_t * ct * skd) + 2.0 * r_t * ct * ckd * omc + omc * omc;
     dr = dr_t - d2 / (rt + r_t);
-    alpha = atan2(b, a);
-    ca = a / rt;
-    sa = b / rt;
+    double ao = a, bo = b;
+    if (off) {
+      // off-surface target y_t + v, v = (v1, v2, v3) in the target's frame (e1, e2, e3)(s_t);
+      // moving along the axis by Delta turns e1, e3 by kappa Delta about e2:
+      //   e1(s_t) = cos e1(s) - sin e3(s),  e3(s_t) = sin e1(s) + cos e3(s)
+      const double va = off[0] * ckd + off[2] * skd, vb = off[1], vc = -off[0] * skd + off[2] * ckd;
+      ao = a + va;
+      bo = b + vb;
+      const double rto = hypot(ao, bo);
+      dr -= (2.0 * (a * va + b * vb) + va * va + vb * vb) / (rto + rt);
+      rt = rto;
+      c += vc;
+    }
+    alpha = atan2(bo, ao);
+    ca = ao / rt;
+    sa = bo / rt;
     const double dl = 0.5 * B.L * cos(s);                                    // l'(s)
     const double rp = drho_prof(B, u) * 0.5 * cos(s) * cos(s) - rho_s * sin(s);  // r'(s)
     a0 = r * dl;
@@ -416,7 +440,8 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
                                                        const qd4* __restrict__ x64, const qd4* __restrict__ n64,
                                                        const double* __restrict__ jac, double k, double eta,
                                                        long long row0, double2* __restrict__ blocks,
-                                                       unsigned long long* __restrict__ counts, int pstride) {
+                                                       unsigned long long* __restrict__ counts, int pstride,
+                                                       const NearTarget* __restrict__ near) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowShared& S = *reinterpret_cast<RowShared*>(smem_raw);
   // Q_{m-1/2} and dQ/dchi of the batch, [BATCH][pstride] each (pstride >= P + 1, even),
@@ -427,24 +452,30 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   double* bdq = bq + BATCH * pstride;
   float4* accD = reinterpret_cast<float4*>(bdq + BATCH * pstride);
 
-  // rows of the assembled bodies (one per class of congruent bodies), back to back
+  // rows of the assembled bodies (one per class of congruent bodies), back to back;
+  // or, with `near`, one off-surface target per CTA (the near-field rows)
   const long long gc = row0 + blockIdx.x;
+  const bool nearm = near != nullptr;
   int lo = 0, hi = nb - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (bodies[mid].crow <= gc) lo = mid; else hi = mid - 1;
+  if (nearm) {
+    lo = near[gc].cls;
+  } else {
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bodies[mid].crow <= gc) lo = mid; else hi = mid - 1;
+    }
   }
   const AsmBody B = bodies[lo];
-  const long long g = B.offset + (gc - B.crow);  // global target node
   const int tid = threadIdx.x;
   const int nth = B.n_theta, N = nth / 2, order = B.order;
   const int per_panel = order * nth;
   float4* accS = accD + per_panel;
   const int nbn = B.n_panels * per_panel;
-  const int t = (int)(g - B.offset);
-  const int p = t / per_panel;
-  const int lt = (t % per_panel) / nth;
-  const int jt = t % nth;
+  const int t = nearm ? -1 : (int)(gc - B.crow);  // target node within the body
+  const int p = nearm ? near[gc].panel : t / per_panel;
+  const int lt = nearm ? 0 : (t % per_panel) / nth;
+  const int jt = nearm ? 0 : t % nth;
+  const double* toff = nearm ? near[gc].v : nullptr;
   const double* gl_x = rules + B.rule;              // [order] on [-1,1]
   const double* dy_x = gl_x + 2 * order;            // [level1_nodes] on [0,1]
   const double* dy_w = dy_x + level1_nodes(order);
@@ -459,15 +490,15 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   const Rules RL{d0_x, d0_w, dy_x, dy_w, g12_x, g12_w, in_x, in_w, ad_x, ad_w};
   const double* bw = g12_w + 12;                    // [order] barycentric weights of the GL nodes
   const double* brk = rules + B.brk;                // panel breakpoints [n_panels + 1]
-  const double s_t = 0.5 * (brk[p] + brk[p + 1]) + 0.5 * (brk[p + 1] - brk[p]) * gl_x[lt];
-  const double th_t = 2.0 * M_PI * jt / nth;
+  const double s_t = nearm ? near[gc].s : 0.5 * (brk[p] + brk[p + 1]) + 0.5 * (brk[p + 1] - brk[p]) * gl_x[lt];
+  const double th_t = nearm ? near[gc].th : 2.0 * M_PI * jt / nth;
   const double inv_nth = 1.0 / nth;
   const bool kz = (k == 0.0);
   const int n1 = kz ? 0 : B.n1;
   const int M = B.M, M2 = M / 2;
   const double twopi_M = 2.0 * M_PI / M;
   const int P = N + n1 + 2;
-  double2* row = blocks + B.blk + (long long)t * nbn;
+  double2* row = nearm ? blocks + near[gc].row : blocks + B.blk + (long long)t * nbn;
 
   for (int e = tid; e < 2 * per_panel; e += NT) accD[e] = make_float4(0.f, 0.f, 0.f, 0.f);
   int n_far = 0;  // thread 0: far outer nodes of this row
@@ -537,7 +568,8 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       S.bw[tid] = wq;
       S.bp[tid] = pq;
       S.bflush[tid] = fq;
-      ring_node(B, rules, s_t, th_t, hq, P, N, S.inv_odd, bq + tid * pstride, bdq + tid * pstride, S.bs[tid]);
+      ring_node(B, rules, s_t, th_t, hq, P, N, S.inv_odd, bq + tid * pstride, bdq + tid * pstride, S.bs[tid],
+                toff);
     }
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
@@ -801,7 +833,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
             if (idx >= nth) idx -= nth;
           }
           double2 v = make_double2(ff_to_double(sr) * inv_nth, ff_to_double(si) * inv_nth);
-          if (base + e == t) v.x += 0.5;
+          if (base + e == t) v.x += 0.5;  // (never for an off-surface target: t < 0)
           row[base + e] = v;
         }
         // add the far-ring part (same entries per thread: e = tid + q NT)
@@ -825,7 +857,31 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
     atomicAdd(&counts[0], (unsigned long long)(nq - n_far));
     atomicAdd(&counts[1], (unsigned long long)n_far);
   }
+  if (nearm) {
+    // near-field row: product integration minus the smooth rule on the near panels
+    // (the caller adds the smooth rule over all nodes), zero beyond them
+    qd4 xt;
+    xt.x = near[gc].x[0];
+    xt.y = near[gc].x[1];
+    xt.z = near[gc].x[2];
+    xt.w = 0.0;
+    const long long node0 = near[gc].node0;
+    for (int e = tid; e < nbn; e += NT) {
+      const int i = e / per_panel;
+      if (abs(i - p) > 1) {
+        row[e] = make_double2(0.0, 0.0);
+        continue;
+      }
+      double kre, kim;
+      const qd4 ys = x64[node0 + e];
+      smooth_kernel(xt, ys, n64[node0 + e], k, eta, &kre, &kim);
+      row[e].x -= kre * ys.w;
+      row[e].y -= kim * ys.w;
+    }
+    return;
+  }
   // panels beyond the neighbours: the plain smooth rule
+  const long long g = B.offset + t;  // global target node
   const qd4 xt = x64[g];
   for (int e = tid; e < nbn; e += NT) {
     const int i = e / per_panel;
@@ -848,13 +904,17 @@ size_t qams_selfblock_smem(int max_per_panel, int pstride) {
   return sizeof(RowShared) + 2 * sizeof(double) * BATCH * (size_t)pstride + 2 * sizeof(float4) * (size_t)max_per_panel;
 }
 
-int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
-  // one block per class of congruent bodies, from its first body's rows
+namespace {
+
+// Kernel tables of the context's classes of congruent bodies (one AsmBody per
+// class, from its first body) and the rule tables per distinct order.  r_extra
+// widens the smooth-factor bandwidth for targets up to r_extra off the surface.
+int build_tables(qams_ctx* c, double r_extra, std::vector<AsmBody>& ab, std::vector<double>& rules, long long* blk_out,
+                 long long* rows_out, int* max_nb_out, int* pstride_out) {
   const int nb = (int)c->class_rep.size();
-  // rule tables per distinct order
-  std::vector<double> rules;
   std::vector<int> rule_off(64, -1);
-  std::vector<AsmBody> ab(nb);
+  ab.assign(nb, AsmBody{});
+  rules.clear();
   long long blk = 0, rows = 0;
   int max_nb = 0, pstride = 0;
   for (int b = 0; b < nb; ++b) {
@@ -923,7 +983,7 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
     rows += bh.n;
     A.blk = blk;
     blk += (long long)bh.n * bh.n;
-    const double rmax = bh.rmax;
+    const double rmax = bh.rmax + r_extra;
     A.n1 = (int)std::ceil(1.3 * c->k * rmax + 16.0);
     A.M = 2 * (A.n1 + 8);
     if (A.n1 + 2 > MAXN1 || A.M / 2 + 1 > MAXM2 || d.n_theta / 2 + A.n1 + 2 > MAXP || A.M > 2 * MAXM2)
@@ -932,7 +992,24 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
     max_nb = std::max(max_nb, d.order * d.n_theta);
     pstride = std::max(pstride, (d.n_theta / 2 + A.n1 + 2 + 1 + 1) & ~1);  // P + 1, rounded up to even
   }
-  int rc;
+  *blk_out = blk;
+  *rows_out = rows;
+  *max_nb_out = max_nb;
+  *pstride_out = pstride;
+  return QAMS_OK;
+}
+
+}  // namespace
+
+int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
+  // one block per class of congruent bodies, from its first body's rows
+  const int nb = (int)c->class_rep.size();
+  std::vector<AsmBody> ab;
+  std::vector<double> rules;
+  long long blk = 0, rows = 0;
+  int max_nb = 0, pstride = 0;
+  int rc = build_tables(c, 0.0, ab, rules, &blk, &rows, &max_nb, &pstride);
+  if (rc) return rc;
   qams_dev_free(c, &c->blocks64);
   if ((rc = qams_dev_alloc(c, &c->blocks64, sizeof(double2) * (size_t)blk))) return rc;
   c->block_entries = blk;
@@ -960,7 +1037,7 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
                                                     (const qd4*)c->x64.p, (const qd4*)c->n64.p,
                                                     (const double*)c->jac64.p, c->k, c->eta, r0,
                                                     (double2*)c->blocks64.p, (unsigned long long*)d_counts.p,
-                                                    pstride); qams_count_launch();
+                                                    pstride, nullptr); qams_count_launch();
     qams_prof_end(c, QAMS_PROF_ASSEMBLY, st, pe);
     QAMS_CUDA(cudaGetLastError());
   }
@@ -972,5 +1049,45 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   qams_dev_free(c, &d_bodies);
   qams_dev_free(c, &d_rules);
   qams_dev_free(c, &d_counts);
+  return QAMS_OK;
+}
+
+// Near-field rows (see selfblock_kernel with `near`): one row of n_b entries per
+// target, at targets[i].row of `rows`, for n targets already on the device.
+int qams_near_rows_launch(qams_ctx* c, const NearTarget* targets, long long n, double r_extra, double2* rows,
+                          cudaStream_t st) {
+  if (n <= 0) return QAMS_OK;
+  const int nb = (int)c->class_rep.size();
+  std::vector<AsmBody> ab;
+  std::vector<double> rules;
+  long long blk = 0, nrows = 0;
+  int max_nb = 0, pstride = 0;
+  int rc = build_tables(c, r_extra, ab, rules, &blk, &nrows, &max_nb, &pstride);
+  if (rc) return rc;
+  DeviceBuf d_bodies, d_rules;
+  if ((rc = qams_dev_alloc(c, &d_bodies, sizeof(AsmBody) * nb))) return rc;
+  if ((rc = qams_dev_alloc(c, &d_rules, sizeof(double) * rules.size()))) {
+    qams_dev_free(c, &d_bodies);
+    return rc;
+  }
+  QAMS_CUDA(cudaMemcpy(d_bodies.p, ab.data(), sizeof(AsmBody) * nb, cudaMemcpyHostToDevice));
+  QAMS_CUDA(cudaMemcpy(d_rules.p, rules.data(), sizeof(double) * rules.size(), cudaMemcpyHostToDevice));
+  const size_t smem = qams_selfblock_smem(max_nb, pstride);
+  const int smem_max = (int)qams_selfblock_smem(MAXORD * 2 * MAXN, MAXP + 2);
+  QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
+  QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  const long long chunk = 1 << 20;
+  for (long long r0 = 0; r0 < n; r0 += chunk) {
+    const long long m = std::min(chunk, n - r0);
+    selfblock_kernel<<<(unsigned)m, NT, smem, st>>>((const AsmBody*)d_bodies.p, nb, (const double*)d_rules.p,
+                                                    (const qd4*)c->x64.p, (const qd4*)c->n64.p,
+                                                    (const double*)c->jac64.p, c->k, c->eta, r0, rows, nullptr,
+                                                    pstride, targets);
+    qams_count_launch();
+    QAMS_CUDA(cudaGetLastError());
+  }
+  QAMS_CUDA(cudaStreamSynchronize(st));
+  qams_dev_free(c, &d_bodies);
+  qams_dev_free(c, &d_rules);
   return QAMS_OK;
 }

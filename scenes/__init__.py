@@ -219,6 +219,54 @@ def reduced(idx: int, n_copies: int) -> Scene:
                  base.directions)
 
 
+@dataclasses.dataclass
+class LatticeScene(Scene):
+    """A regular array of one body: ``dims`` copies along the rows of
+    ``basis`` (Sec. 4, regular P x Q x R arrays); ``bodies`` lists them in
+    the order p, q, r (body index (p Q + q) R + r)."""
+    body: Optional[Body] = None
+    dims: tuple = (1, 1, 1)
+    basis: Optional[np.ndarray] = None
+
+
+def lattice_scene(name: str, body: Body, dims, basis, k: float, eta: float,
+                  directions: np.ndarray) -> LatticeScene:
+    basis = np.asarray(basis, dtype=np.float64).reshape(3, 3)
+    c0 = np.asarray(body.center, dtype=np.float64)
+    bodies = []
+    for p in range(dims[0]):
+        for q in range(dims[1]):
+            for r in range(dims[2]):
+                c = c0 + p * basis[0] + q * basis[1] + r * basis[2]
+                bodies.append(dataclasses.replace(body, center=tuple(float(v) for v in c)))
+    return LatticeScene(name, bodies, k, eta, directions, body=body, dims=tuple(int(v) for v in dims),
+                        basis=basis)
+
+
+def paper_cubic(P: int = 10, k: float = 2.0, order: int = 16, n_theta: int = 6) -> LatticeScene:
+    """P^3 quasi-ellipsoids (Eq. quasiellipsoid) on a cubic lattice of spacing
+    0.5, the regular-array experiment of Sec. 6 (Table tab:multibody_cubic:
+    N_p = 1, 16 x N_f = 6 nodes, 10^3 bodies in [-1, 4]^3, surface gaps above
+    0.05).  Reading: the scale 0.04 keeps bounding balls 0.087 apart; the
+    incident direction is the paper's d(pi/3, 2 pi/3)."""
+    b = quasi_ellipsoid(1, order, n_theta, scale=0.04, center=(-0.75, -0.75, -0.75))
+    return lattice_scene(f"{P}^3 quasi-ellipsoids, 16x{n_theta} nodes, k={k:g}", b, (P, P, P),
+                         0.5 * np.eye(3), k, 1.0, paper_direction())
+
+
+def lattice_of_workload(idx: int, dims=(10, 10, 10), gap: float = 0.5) -> LatticeScene:
+    """The first seeded body of workload ``idx`` repeated on a cubic lattice
+    whose bounding balls are ``gap`` apart, with that workload's wavenumber
+    and incident directions (e.g. 10^3 copies of the 1000-body workload's
+    body: the same N = 512,000, k = 3 and 4 right-hand sides, in the
+    translation-invariant arrangement of Sec. 4)."""
+    base = config(idx)
+    b0 = dataclasses.replace(base.bodies[0], center=(0.0, 0.0, 0.0))
+    h = 2.0 * b0.bound_radius() + gap
+    return lattice_scene(f"{dims[0]}x{dims[1]}x{dims[2]} lattice of body 0 of workload {idx} ({base.name})", b0,
+                         dims, h * np.eye(3), base.k, base.eta, base.directions)
+
+
 def small_scene(n_bodies: int = 3, n_panels: int = 1, order: int = 8, n_theta: int = 16,
                 k: float = 2.0, eta: float = 1.0, n_rhs: int = 1, seed: int = 7,
                 box: float = 6.0) -> Scene:

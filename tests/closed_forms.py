@@ -62,3 +62,17 @@ def point_source_farfield(xhat, z, k: float):
     for zl in np.atleast_2d(z):
         out += np.exp(-1j * k * (xhat @ zl)) / (4 * np.pi)
     return out
+
+
+def sphere_layer_potentials(a: float, k: float, n: int, r: float):
+    """(s_n, d_n): single- and double-layer potentials of a degree-n
+    spherical harmonic density Y on the sphere of radius a, at radius r != a,
+    are s_n Y(xhat) and d_n Y(xhat) (addition theorem for G):
+        r > a:  s_n = ik a^2 j_n(ka) h_n(kr),   d_n = ik^2 a^2 j_n'(ka) h_n(kr),
+        r < a:  s_n = ik a^2 h_n(ka) j_n(kr),   d_n = ik^2 a^2 h_n'(ka) j_n(kr)."""
+    ka, kr = k * a, k * r
+    if r > a:
+        return (1j * k * a * a * sp.spherical_jn(n, ka) * _h(n, kr),
+                1j * k * k * a * a * sp.spherical_jn(n, ka, True) * _h(n, kr))
+    return (1j * k * a * a * _h(n, ka) * sp.spherical_jn(n, kr),
+            1j * k * k * a * a * _h(n, ka, True) * sp.spherical_jn(n, kr))

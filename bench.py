@@ -336,6 +336,8 @@ def run_lattice(q, torch, sc, steps, warmup, tol, local_rank):
     torch.cuda.synchronize()
     elapsed = t0.elapsed_time(t1) / 1e3
     nlat, ms_lat = ctx.profile_read(q.PROF_PAIRSUM_LATTICE)
+    np32, ms32 = ctx.profile_read(q.PROF_LATTICE_PRODUCT32)
+    np64, ms64 = ctx.profile_read(q.PROF_LATTICE_PRODUCT64)
     ctx.profile(False)
     applies = [r[1]["applies_fp32"] + r[1]["applies_fp64"] for r in recs]
     pairs = sc.pair_count()
@@ -343,6 +345,19 @@ def run_lattice(q, torch, sc, steps, warmup, tol, local_rank):
     out = summary(w, steps, 1)
     out["workload"] = sc.name
     out["lattice_pairsum_ms_per_apply"] = ms_lat / max(nlat, 1)
+    # the per-frequency products stream the transformed blocks: (2P-1)(2Q-1)(2R-1) n^2 entries
+    F = 1
+    for p_ in sc.dims:
+        F *= 2 * p_ - 1
+    n = sc.body.n_nodes
+    hbm = measured_peaks()[0]["hbm_gbs"]
+    prods = {}
+    for name, cnt, ms, eb in (("complex64", np32, ms32, 8), ("complex128", np64, ms64, 16)):
+        if cnt:
+            gbs = F * n * n * eb / (ms / cnt / 1e3) / 1e9
+            prods[name] = {"launches": cnt, "ms_per_launch": ms / cnt, "algorithmic_bytes": F * n * n * eb,
+                           "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "bound": "hbm"}
+    out["freq_product_kernel"] = prods
     # independent check: the residual under the direct float-float operator
     ctx.set_option(q.OPT_LATTICE, 0)
     y = torch.empty_like(mu)
@@ -702,6 +717,9 @@ def main():
                     help="Poisson arrival rates as fractions of the saturated rate")
     ap.add_argument("--serve-sample", type=int, default=8,
                     help="requests of the serving distribution measured in the default run (0: none)")
+    ap.add_argument("--lattice", choices=["workload", "paper"], default=None,
+                    help="time solves of a regular array instead (10^3 copies of the 1000-body workload's body, "
+                         "or the paper's 10^3 quasi-ellipsoids at k = 5) and print one JSON line")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
@@ -709,6 +727,17 @@ def main():
     if args.serve:
         if rank == 0:
             run_serve(args)
+    elif args.lattice and args.impl == "ours":
+        if rank == 0:
+            import torch
+
+            import paper_2606_31380_b300 as q
+            import scenes
+            sc = scenes.lattice_of_workload(3) if args.lattice == "workload" else scenes.paper_cubic(10, 5.0)
+            out = run_lattice(q, torch, sc, args.steps, args.warmup, args.tol, local_rank)
+            out.update({"metric": METRIC, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+                        "n_gpus": 1, "higher_is_better": True, "data": "synthetic (regular array)"})
+            print(json.dumps(out), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

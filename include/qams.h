@@ -127,7 +127,9 @@ enum {
   QAMS_PROF_BLOCK_TC = 6,     /* self-block / preconditioner products on the tensor cores */
   QAMS_PROF_PAIRSUM_TC = 7,   /* FP32 pair sum with its accumulation on the tensor cores */
   QAMS_PROF_PAIRSUM_LATTICE = 8, /* pair sum of a lattice through the circulant embedding (all passes) */
-  QAMS_PROF_COUNT = 9
+  QAMS_PROF_LATTICE_PRODUCT32 = 9,  /* its per-frequency products, complex64 */
+  QAMS_PROF_LATTICE_PRODUCT64 = 10, /* its per-frequency products, complex128 */
+  QAMS_PROF_COUNT = 11
 };
 int qams_profile_enable(qams_ctx* ctx, int on);
 int qams_profile_read(qams_ctx* ctx, int slot, long long* launches, double* total_ms);

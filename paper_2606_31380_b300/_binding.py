@@ -15,7 +15,7 @@ PREC_FP32 = 1
 PREC_FF = 2  # float-float pair sum on complex128 data
 # launch-timing slots (qams_profile_read)
 PROF_PAIRSUM_FP32, PROF_PAIRSUM_FF, PROF_PAIRSUM_FP64, PROF_BLOCK_FP32, PROF_BLOCK_FP64, PROF_ASSEMBLY, \
-    PROF_BLOCK_TC, PROF_PAIRSUM_TC, PROF_PAIRSUM_LATTICE = range(9)
+    PROF_BLOCK_TC, PROF_PAIRSUM_TC, PROF_PAIRSUM_LATTICE, PROF_LATTICE_PRODUCT32, PROF_LATTICE_PRODUCT64 = range(11)
 OPT_TC_MIN_RHS, OPT_TC_PAIR_MIN_RHS, OPT_PAIR_TARGETS, OPT_LATTICE, OPT_NEAR_FIELD = 0, 1, 2, 3, 4  # option keys
 
 

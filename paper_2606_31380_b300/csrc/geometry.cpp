@@ -267,7 +267,7 @@ extern "C" int qams_body_nodes(const qams_body_desc* desc, double* x_host, doubl
 }
 
 void qams_nearest_point(const BodyHost& b, const double* hx_body, const double x[3], double* s_out,
-                        double* th_out, int* panel_out, double* dist_out, double v_out[3]) {
+                        double* th_out, int* panel_out, double* dist_out, double* ds_out, double v_out[3]) {
   const qams_body_desc& d = b.d;
   Shape sh{b};
   // body-local target
@@ -338,6 +338,17 @@ void qams_nearest_point(const BodyHost& b, const double* hx_body, const double x
   double v[3];
   for (int q = 0; q < 3; ++q) v[q] = xl[q] - p[q];
   *dist_out = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  {
+    // |d_s y| by a central difference: the distance in units of s
+    double pa[3], pb[3], dummy;
+    const double hs = 1e-6, sa = std::min(smax, s + hs), sb = std::max(-smax, s - hs);
+    sh.eval(sa, th, pa, nn, &dummy);
+    sh.eval(sb, th, pb, nn, &dummy);
+    double sp = 0.0;
+    for (int q = 0; q < 3; ++q) sp += (pa[q] - pb[q]) * (pa[q] - pb[q]);
+    sp = std::sqrt(sp) / (sa - sb);
+    *ds_out = sp > 0.0 ? *dist_out / sp : *dist_out;
+  }
   if (d.profile_kind == 1) {
     for (int q = 0; q < 3; ++q) v_out[q] = v[q];
   } else {

@@ -18,12 +18,16 @@
 // 3-D discrete Fourier transform diagonalises:
 //   y = IDFT_f( T^(f) DFT(sigma)(f) ),  T^(f) = sum_d T(d) e^{-2 pi i f.d/L},
 // one dense n x n by n x R product per frequency f.  T^ is formed once per
-// wavenumber in FP64 (kept in complex128 and rounded to complex64); an apply
+// wavenumber (kernel values in FP64, the transform in float-float; kept in
+// complex128 and rounded to complex64); an apply
 // is three DFT passes over the zero-padded densities, the frequency
 // products, and three inverse passes cropped to the lattice.  The DFTs are
 // direct sums along one axis at a time (L_k <= 63), staged in shared memory.
+#include <algorithm>
 #include <cmath>
 
+#include "ffloat.cuh"
+#include "phase.cuh"
 #include "qams_internal.h"
 
 namespace {
@@ -50,6 +54,9 @@ __global__ void lattice_blocks_kernel(const qd4* __restrict__ x64, const qd4* __
                                       const qd4* __restrict__ centers, int n, int L0, int L1, int L2, int P0,
                                       int P1, int P2, double3 a0, double3 a1, double3 a2, double k, double eta,
                                       double2* __restrict__ T) {
+  __shared__ double2 ptab[PH_N];
+  phase_table_fill(ptab);
+  __syncthreads();
   const long long nn = (long long)n * n;
   const long long total = (long long)L0 * L1 * L2 * nn;
   const qd4 c0 = centers[0];
@@ -74,7 +81,7 @@ __global__ void lattice_blocks_kernel(const qd4* __restrict__ x64, const qd4* __
     const double inv = 1.0 / rho;
     const double nd = -(nj.x * rx + nj.y * ry + nj.z * rz);  // n_s . (y_s - x_t)
     double s, c;
-    sincos(k * rho, &s, &c);
+    sincos_table(k * rho, ptab, &s, &c);
     const double g = inv * inv4pi;
     const double bre = -nd * inv * inv, bim = k * nd * inv - eta;
     T[idx] = make_double2(g * (c * bre - s * bim), g * (c * bim + s * bre));
@@ -142,45 +149,150 @@ __global__ void __launch_bounds__(DFT_THREADS) axis_dft_kernel(const T2* in, T2*
   }
 }
 
-// Frequency products: one warp per row (f, i),
-//   y[f][i][r0 + r] = sum_j A[f][i][j] x[f][j][r0 + r],  r < RC.
-template <typename T2, int RC>
-__global__ void freq_product_kernel(const T2* __restrict__ A, const T2* __restrict__ x, T2* __restrict__ y,
-                                    long long rows, int n, int R, int r0) {
-  using F = typename Real<T2>::T;
-  const long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= rows) return;
-  const long long f = row / n;
-  const T2* a = A + row * n;
-  const T2* xf = x + f * n * R + r0;
-  F ar[RC], ai[RC];
-#pragma unroll
-  for (int r = 0; r < RC; ++r) ar[r] = ai[r] = F(0);
-  for (int j = lane; j < n; j += 32) {
-    const T2 v = a[j];
-    const T2* xv = xf + (long long)j * R;
-#pragma unroll
-    for (int r = 0; r < RC; ++r) {
-      const T2 u = xv[r];
-      ar[r] += v.x * u.x - v.y * u.y;
-      ai[r] += v.x * u.y + v.y * u.x;
-    }
+// The same pass on complex128 data with the sums in float-float arithmetic
+// (pairs of FP32, ~48 bits) on the FP32 pipe: the transform of the displacement
+// blocks, where FP64 issue (1/64 of FP32 on this GPU) would bound the prepare.
+__global__ void __launch_bounds__(DFT_THREADS) axis_dft_ff_kernel(const double2* in, double2* out, AxisPass p,
+                                                                  const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float4* s = reinterpret_cast<float4*>(smraw);  // [Jin][CB] (re hi, re lo, im hi, im lo)
+  float4* stw = s + p.Jin * CB;                  // [L]
+  const int line = blockIdx.y;
+  const int a0 = line / p.n_a1, a1 = line - (line / p.n_a1) * p.n_a1;
+  const long long b0 = (long long)blockIdx.x * CB;
+  const long long ibase = a0 * p.is0 + a1 * p.is1 + b0, obase = a0 * p.os0 + a1 * p.os1 + b0;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < p.Jin * CB; idx += DFT_THREADS) {
+    const int j = idx / CB, cc = idx - (idx / CB) * CB;
+    double2 v = make_double2(0.0, 0.0);
+    if (b0 + cc < p.B) v = in[ibase + j * p.iB + cc];
+    const ff re = ff_from_double(v.x), im = ff_from_double(v.y);
+    s[idx] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
-#pragma unroll
-  for (int r = 0; r < RC; ++r)
-    for (int o = 16; o > 0; o >>= 1) {
-      ar[r] += __shfl_xor_sync(0xffffffffu, ar[r], o);
-      ai[r] += __shfl_xor_sync(0xffffffffu, ai[r], o);
+  for (int m = tid; m < p.L; m += DFT_THREADS) {
+    const ff c = ff_from_double(tw[m].x), sn = ff_from_double(tw[m].y);
+    stw[m] = make_float4(c.hi, c.lo, sn.hi, sn.lo);
+  }
+  __syncthreads();
+  const int cc = tid & (CB - 1), g = tid / CB;
+  if (b0 + cc >= p.B) return;
+  for (int f = g; f < p.Jout; f += DFT_THREADS / CB) {
+    ff ar{0.f, 0.f}, ai{0.f, 0.f};
+    int m = 0;
+    for (int j = 0; j < p.Jin; ++j) {
+      const float4 v = s[j * CB + cc], w = stw[m];
+      const ff vr{v.x, v.y}, vi{v.z, v.w}, wr{w.x, w.y}, wi{w.z, w.w};
+      ar = ff_add(ar, ff_sub(ff_mul(vr, wr), ff_mul(vi, wi)));
+      ai = ff_add(ai, ff_add(ff_mul(vr, wi), ff_mul(vi, wr)));
+      m += f;
+      if (m >= p.L) m -= p.L;
     }
-  if (lane == 0) {
-    T2* yv = y + row * R + r0;
+    out[obase + f * p.oB + cc] = make_double2(ff_to_double(ar), ff_to_double(ai));
+  }
+}
+
+int run_pass_ff(const double2* in, double2* out, const AxisPass& p, const double2* tw, cudaStream_t st) {
+  if (p.n_a0 * (long long)p.n_a1 > 65535 || p.B <= 0) return QAMS_EINVAL;
+  const dim3 grid((unsigned)((p.B + CB - 1) / CB), (unsigned)(p.n_a0 * p.n_a1));
+  const size_t smem = sizeof(float4) * ((size_t)p.Jin * CB + p.L);
+  axis_dft_ff_kernel<<<grid, DFT_THREADS, smem, st>>>(in, out, p, tw);
+  qams_count_launch();
+  QAMS_CUDA(cudaGetLastError());
+  return QAMS_OK;
+}
+
+// Frequency products, one CTA per frequency f: x[f][:, r0..r0+RC) is staged in
+// shared memory transposed ([r][j], so consecutive lanes read consecutive
+// words), then one warp per row i streams A[f][i][:] from HBM (U loads in flight
+// per lane; complex64 rows as pairs of entries, 16 bytes per lane) against it,
+//   y[f][i][r0 + r] = sum_j A[f][i][j] x[f][j][r0 + r],  r < RC.
+constexpr int FP_THREADS = 256;
+
+template <typename F>
+__device__ __forceinline__ void cmac(F& ar, F& ai, F vx, F vy, F wx, F wy) {
+  ar += vx * wx - vy * wy;
+  ai += vx * wy + vy * wx;
+}
+
+template <typename T2, int RC>
+__global__ void __launch_bounds__(FP_THREADS) freq_product_kernel(const T2* __restrict__ A, const T2* __restrict__ x,
+                                                                  T2* __restrict__ y, int n, int R, int r0) {
+  using F = typename Real<T2>::T;
+  constexpr int U = RC >= 8 ? 2 : 4;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T2* xs = reinterpret_cast<T2*>(smraw);  // [RC][n]
+  const long long f = blockIdx.x;
+  const T2* xf = x + f * n * R + r0;
+  for (int e = threadIdx.x; e < n * RC; e += FP_THREADS) {
+    const int j = e / RC, r = e - (e / RC) * RC;
+    xs[r * n + j] = xf[(long long)j * R + r];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < n; i += FP_THREADS / 32) {
+    F ar[RC], ai[RC];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) {
-      T2 v;
-      v.x = ar[r];
-      v.y = ai[r];
-      yv[r] = v;
+    for (int r = 0; r < RC; ++r) ar[r] = ai[r] = F(0);
+    if constexpr (sizeof(T2) == sizeof(float2)) {
+      // n is even (an even number of azimuths), so rows are 16-byte aligned pairs
+      const float4* a = reinterpret_cast<const float4*>(A + (f * n + i) * n);
+      const int n2 = n >> 1;
+      for (int j0 = lane; j0 < n2; j0 += 32 * U) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = j0 + 32 * u < n2 ? a[j0 + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j2 = j0 + 32 * u;
+          if (j2 >= n2) break;
+#pragma unroll
+          for (int r = 0; r < RC; ++r) {
+            const float4 w = *reinterpret_cast<const float4*>(xs + r * n + 2 * j2);
+            cmac(ar[r], ai[r], v[u].x, v[u].y, w.x, w.y);
+            cmac(ar[r], ai[r], v[u].z, v[u].w, w.z, w.w);
+          }
+        }
+      }
+    } else {
+      const T2* a = A + (f * n + i) * n;
+      for (int j0 = lane; j0 < n; j0 += 32 * U) {
+        T2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (j0 + 32 * u < n) {
+            v[u] = a[j0 + 32 * u];
+          } else {
+            v[u].x = F(0);
+            v[u].y = F(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = j0 + 32 * u;
+          if (j >= n) break;
+#pragma unroll
+          for (int r = 0; r < RC; ++r) {
+            const T2 w = xs[r * n + j];
+            cmac(ar[r], ai[r], v[u].x, v[u].y, w.x, w.y);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RC; ++r)
+      for (int o = 16; o > 0; o >>= 1) {
+        ar[r] += __shfl_xor_sync(0xffffffffu, ar[r], o);
+        ai[r] += __shfl_xor_sync(0xffffffffu, ai[r], o);
+      }
+    if (lane == 0) {
+      T2* yv = y + (f * n + i) * R + r0;
+#pragma unroll
+      for (int r = 0; r < RC; ++r) {
+        T2 w;
+        w.x = ar[r];
+        w.y = ai[r];
+        yv[r] = w;
+      }
     }
   }
 }
@@ -213,10 +325,17 @@ const T2* twiddles(const qams_ctx* c, int ax, int dir) {
 }
 
 template <typename T2, int RC>
-void launch_product(const T2* A, const T2* x, T2* y, long long rows, int n, int R, int r0, cudaStream_t st) {
-  const long long threads = rows * 32;
-  freq_product_kernel<T2, RC><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, x, y, rows, n, R, r0);
+int launch_product(const T2* A, const T2* x, T2* y, long long F, int n, int R, int r0, cudaStream_t st) {
+  const size_t smem = sizeof(T2) * (size_t)n * RC;
+  if (smem > 48 * 1024) {
+    if (smem > 227 * 1024) return QAMS_EINVAL;
+    QAMS_CUDA(cudaFuncSetAttribute(freq_product_kernel<T2, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  }
+  freq_product_kernel<T2, RC><<<(unsigned)F, FP_THREADS, smem, st>>>(A, x, y, n, R, r0);
   qams_count_launch();
+  QAMS_CUDA(cudaGetLastError());
+  return QAMS_OK;
 }
 
 template <typename T2>
@@ -246,17 +365,23 @@ int lattice_apply(qams_ctx* c, int R, const T2* sigma, T2* y, const T2* that, cu
   p = AxisPass{(long long)L1 * L2 * nR, 1, 1, 0, 0, (long long)L1 * L2 * nR, 0, 0, (long long)L1 * L2 * nR, P0, L0, L0};
   if ((rc = run_pass<T2>(w, w, p, twiddles<T2>(c, 0, 0), 1.0, st))) return rc;
   // products per frequency
+  const int pslot = sizeof(T2) == sizeof(double2) ? QAMS_PROF_LATTICE_PRODUCT64 : QAMS_PROF_LATTICE_PRODUCT32;
+  // right-hand sides per product launch: staged columns fit in 200 KB of shared memory
+  const int max_rc = (int)std::min<long long>(16, (200LL * 1024) / ((long long)n * (long long)sizeof(T2)));
+  if (max_rc < 1) return QAMS_EINVAL;
   for (int r0 = 0; r0 < R;) {
-    const int left = R - r0;
+    const int left = std::min(R - r0, max_rc);
     const int rcn = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+    cudaEvent_t pe = qams_prof_begin(c, pslot, st);
     switch (rcn) {
-      case 16: launch_product<T2, 16>(that, w, w2, F * n, n, R, r0, st); break;
-      case 8: launch_product<T2, 8>(that, w, w2, F * n, n, R, r0, st); break;
-      case 4: launch_product<T2, 4>(that, w, w2, F * n, n, R, r0, st); break;
-      case 2: launch_product<T2, 2>(that, w, w2, F * n, n, R, r0, st); break;
-      default: launch_product<T2, 1>(that, w, w2, F * n, n, R, r0, st); break;
+      case 16: rc = launch_product<T2, 16>(that, w, w2, F, n, R, r0, st); break;
+      case 8: rc = launch_product<T2, 8>(that, w, w2, F, n, R, r0, st); break;
+      case 4: rc = launch_product<T2, 4>(that, w, w2, F, n, R, r0, st); break;
+      case 2: rc = launch_product<T2, 2>(that, w, w2, F, n, R, r0, st); break;
+      default: rc = launch_product<T2, 1>(that, w, w2, F, n, R, r0, st); break;
     }
-    QAMS_CUDA(cudaGetLastError());
+    qams_prof_end(c, pslot, st, pe);
+    if (rc) return rc;
     r0 += rcn;
   }
   // inverse: axis 0, axis 1 (in place, cropped), axis 2 (-> y, scaled)
@@ -316,12 +441,12 @@ int qams_lattice_prepare_launch(qams_ctx* c, cudaStream_t st) {
   const int L0 = L.L[0], L1 = L.L[1], L2 = L.L[2];
   AxisPass p{nn, L0, L1, (long long)L1 * L2 * nn, (long long)L2 * nn, nn,
              (long long)L1 * L2 * nn, (long long)L2 * nn, nn, L2, L2, L2};
-  if ((rc = run_pass<double2>(T, T, p, twiddles<double2>(c, 2, 0), 1.0, st))) return rc;
+  if ((rc = run_pass_ff(T, T, p, twiddles<double2>(c, 2, 0), st))) return rc;
   p = AxisPass{(long long)L2 * nn, L0, 1, (long long)L1 * L2 * nn, 0, (long long)L2 * nn,
                (long long)L1 * L2 * nn, 0, (long long)L2 * nn, L1, L1, L1};
-  if ((rc = run_pass<double2>(T, T, p, twiddles<double2>(c, 1, 0), 1.0, st))) return rc;
+  if ((rc = run_pass_ff(T, T, p, twiddles<double2>(c, 1, 0), st))) return rc;
   p = AxisPass{(long long)L1 * L2 * nn, 1, 1, 0, 0, (long long)L1 * L2 * nn, 0, 0, (long long)L1 * L2 * nn, L0, L0, L0};
-  if ((rc = run_pass<double2>(T, T, p, twiddles<double2>(c, 0, 0), 1.0, st))) return rc;
+  if ((rc = run_pass_ff(T, T, p, twiddles<double2>(c, 0, 0), st))) return rc;
   round_kernel<<<grid_for(entries), 256, 0, st>>>(T, (float2*)L.that32.p, entries);
   qams_count_launch();
   QAMS_CUDA(cudaGetLastError());

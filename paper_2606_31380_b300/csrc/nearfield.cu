@@ -93,7 +93,7 @@ int qams_near_correction(qams_ctx* c, int R, const void* mu, int M, const double
       if (dx * dx + dy * dy + dz * dz > (B.radius + dnear) * (B.radius + dnear)) continue;
       NearTarget t{};
       double dist;
-      qams_nearest_point(B, c->hx.data() + 3 * B.offset, x, &t.s, &t.th, &t.panel, &dist, t.v);
+      qams_nearest_point(B, c->hx.data() + 3 * B.offset, x, &t.s, &t.th, &t.panel, &dist, &t.ds, t.v);
       if (!(dist < dnear)) continue;
       t.cls = c->body_class[b];
       for (int q = 0; q < 3; ++q) t.x[q] = x[q];

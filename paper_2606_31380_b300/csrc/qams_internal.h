@@ -60,7 +60,7 @@ struct BodyHost : BodyCopy {
 // frame the self-block kernel takes target offsets in (arc axis: (e1, e2,
 // e3)(s); ring-series shapes: the body frame).
 void qams_nearest_point(const BodyHost& b, const double* hx_body, const double x[3], double* s, double* th,
-                        int* panel, double* dist, double v[3]);
+                        int* panel, double* dist, double* ds, double v[3]);
 
 // One target tile of the pair sum: up to TILE consecutive nodes of one body.
 struct TargetTile {
@@ -238,7 +238,8 @@ struct NearTarget {
   int cls;          // class of congruent bodies (index into class_rep)
   int panel;        // panel holding s
   double s, th;     // closest surface point
-  double v[3];      // offset nu n^
+  double ds;        // distance to the surface in units of s (|x - y| / |d_s y|)
+  double v[3];      // offset x - y(s, th)
   double x[3];      // world position (for the smooth-rule subtraction)
   long long node0;  // first node of the body
   long long row;    // first entry of the target's row in the output

@@ -36,6 +36,7 @@
 #include <cmath>
 
 #include "ffloat.cuh"
+#include "phase.cuh"
 #include "qams_internal.h"
 
 namespace {
@@ -47,6 +48,7 @@ constexpr int MAXM2 = 72;    // M/2 + 1 samples of the smooth factors
 constexpr int MAXN1 = 64;    // highest smooth-factor mode + 2 (k r_max up to ~35)
 constexpr int MAXN = 32;     // N = n_theta / 2
 constexpr int MAXORD = 19;
+constexpr int MILLER_MAX = 768;  // start indices of Miller's recurrence (tabulated coefficients)
 constexpr int MAXE = (MAXORD * 2 * MAXN + NT - 1) / NT;  // panel entries per thread
 
 // The outer nodes of a row come in at most four pieces (the self panel split
@@ -55,7 +57,7 @@ constexpr int MAXE = (MAXORD * 2 * MAXN + NT - 1) / NT;  // panel entries per th
 // descriptors when a batch needs them.
 struct alignas(16) RowShared {
   double pc_h0[4], pc_L[4];     // piece start (offset from s_t) and signed length
-  int pc_K[4], pc_panel[4], pc_self[4], pc_end[4];  // levels, panel, self flag, cumulative node count
+  int pc_K[4], pc_panel[4], pc_self[4], pc_end[4];  // levels, panel, u^6-graded innermost, cumulative node count
   int npc, nq;
   // per-batch node data (filled by warp 0; Q and dQ/dchi live in dynamic shared memory)
   double bs[BATCH][18];         // scalars
@@ -138,10 +140,12 @@ __device__ void agm_KE(double mu, double mu_c, double* K, double* E) {
   *E = *K * (1.0 - s);
 }
 
-// cos x, sin(x)/x and (x cos x - sin x)/x^3 from one sincos (Taylor series near 0)
-__device__ __forceinline__ void smooth_factors(double x, double* c, double* sinc, double* q3) {
+// cos x, sin(x)/x and (x cos x - sin x)/x^3 from one sincos (accurate-table method of
+// phase.cuh with the table `ptab` in global memory; Taylor series near 0)
+__device__ __forceinline__ void smooth_factors(double x, const double2* __restrict__ ptab, double* c, double* sinc,
+                                               double* q3) {
   double sn, cs;
-  sincos(x, &sn, &cs);
+  sincos_table(x, ptab, &sn, &cs);
   *c = cs;
   const double ax = fabs(x);
   if (ax < 0.5) {
@@ -339,18 +343,30 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
       f2n3 += 2.0;
     }
   } else {
-    // Miller's start: its error at index n <= P decays like e^{-2 (n_start - n) eta}
-    // (minimal against dominant solution), so P + 10 + 20/eta leaves e^{-40}
-    const int n_start = P + 10 + (int)ceil(20.0 / eta);
-    double rho = 0.0;
-    double fn1 = n_start - 1, f2n1 = 2 * n_start - 1;  // n - 1 and 2n - 1
+    // Miller's algorithm: the backward recurrence
+    //   q_{n-2} = alpha_n chi q_{n-1} - beta_n q_n,  alpha_n = 4(n-1)/(2n-3), beta_n = (2n-1)/(2n-3)
+    // (coefficients tabulated at the head of `tab`: no division in the loop) from
+    // q_{n_start} = 0, q_{n_start-1} = 1, rescaled by 2^-600 whenever it passes 2^600, then
+    // normalised by q_0 = mu K.  The error at index n <= P decays like e^{-2 (n_start - n) eta}
+    // (minimal against dominant solution), so n_start = P + 10 + 20/eta leaves e^{-40}
+    // (eta P > 3 here, so n_start < P + 11 + 20 P/3 < MILLER_MAX).
+    int n_start = P + 10 + (int)ceil(20.0 / eta);
+    if (n_start > MILLER_MAX - 1) n_start = MILLER_MAX - 1;
+    double qn = 0.0, qn1 = 1.0;  // q_n, q_{n-1}
     for (int n = n_start; n >= 2; --n) {
-      rho = (f2n1 - 2.0) / (4.0 * fn1 * chi - f2n1 * rho);
-      if (n - 1 <= P) q[n - 1] = rho;  // ratio q_{n-1}/q_{n-2}
-      fn1 -= 1.0;
-      f2n1 -= 2.0;
+      const double qm = tab[2 * n] * chi * qn1 - tab[2 * n + 1] * qn;  // q_{n-2}
+      qn = qn1;
+      qn1 = qm;
+      if (n - 2 <= P) q[n - 2] = qm;
+      if ((__double2hiint(qm) & 0x7fffffff) > 0x65700000) {  // |q| > 2^600
+        qn *= 0x1p-600;
+        qn1 *= 0x1p-600;
+        for (int m = max(n - 2, 0); m <= P; ++m) q[m] *= 0x1p-600;
+      }
     }
-    for (int n = 1; n <= P; ++n) q[n] = q[n - 1] * q[n];
+    const double s0 = q[0] != 0.0 ? mu * K / q[0] : 0.0;
+    for (int n = 1; n <= P; ++n) q[n] *= s0;
+    q[0] = mu * K;
   }
   const double half_inv = 0.5 / (delta * (2.0 + delta));  // 1 / (2 (chi^2 - 1))
   for (int m = 0; m <= P; ++m) {
@@ -360,13 +376,13 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
 }
 
 // plain smooth combined-layer kernel (far panels of the same body)
-__device__ void smooth_kernel(const qd4& x, const qd4& y, const qd4& n, double k, double eta, double* kre,
-                              double* kim) {
+__device__ void smooth_kernel(const qd4& x, const qd4& y, const qd4& n, double k, double eta,
+                              const double2* __restrict__ ptab, double* kre, double* kim) {
   const double dx = y.x - x.x, dy = y.y - x.y, dz = y.z - x.z;
   const double r2 = dx * dx + dy * dy + dz * dz;
   const double rinv = rsqrt(r2);
   double sn, cs;
-  sincos(k * r2 * rinv, &sn, &cs);
+  sincos_table(k * r2 * rinv, ptab, &sn, &cs);
   const double nyx = n.x * dx + n.y * dy + n.z * dz;
   const double are = -nyx * rinv * rinv, aim = k * nyx * rinv - eta;
   const double f = rinv * 0.079577471545947667884;
@@ -489,6 +505,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   const double* g12_w = g12_x + 12;
   const Rules RL{d0_x, d0_w, dy_x, dy_w, g12_x, g12_w, in_x, in_w, ad_x, ad_w};
   const double* bw = g12_w + 12;                    // [order] barycentric weights of the GL nodes
+  const double2* ptab = reinterpret_cast<const double2*>(rules + 2 * MILLER_MAX);  // (cos, sin)(2 pi j/PH_N)
   const double* brk = rules + B.brk;                // panel breakpoints [n_panels + 1]
   const double s_t = nearm ? near[gc].s : 0.5 * (brk[p] + brk[p + 1]) + 0.5 * (brk[p + 1] - brk[p]) * gl_x[lt];
   const double th_t = nearm ? near[gc].th : 2.0 * M_PI * jt / nth;
@@ -528,12 +545,17 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
         if (i == p) K = max(5, (int)ceil(log2(aL / (0.5 * dpole))));
         else K = max(6, (int)ceil(log2(aL / (3.2 * fabs(h0)))));
         K = min(K, 14);
-        nq += level0_nodes(order) + level1_nodes(order) + 12 * (K - 2) + (i == p ? 20 : 16);
+        // off-surface target at distance ds (in s) from s_t: the integrand is smooth on
+        // the scale ds, so the self panel's levels continue until the innermost piece is
+        // about ds long, which then takes the mildly graded (u^2) rule
+        const bool graded6 = (i == p) && !nearm;
+        if (nearm && i == p) K = min(44, max(K, (int)ceil(log2(aL / fmax(near[gc].ds, 1e-13))) + 1));
+        nq += level0_nodes(order) + level1_nodes(order) + 12 * (K - 2) + (graded6 ? 20 : 16);
         S.pc_h0[npc] = h0;
         S.pc_L[npc] = L;
         S.pc_K[npc] = K;
         S.pc_panel[npc] = i;
-        S.pc_self[npc] = i == p;
+        S.pc_self[npc] = graded6;
         S.pc_end[npc] = nq;
         ++npc;
       }
@@ -605,7 +627,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
           const double inv = rsqrt(rho2), rho = rho2 * inv;
           const double radial = dr + 2.0 * rt * s2;  // r - r~ cos(phi)
           double sn, cs;
-          sincos(k * rho, &sn, &cs);
+          sincos_table(k * rho, ptab, &sn, &cs);
           const double f = 0.079577471545947667884 * inv;
           const double gr = cs * f, gi = sn * f;                               // G
           const double dpr = (-cs - k * rho * sn) * f * inv * inv, dpi = (k * rho * cs - sn) * f * inv * inv;  // G'/rho
@@ -652,7 +674,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
         for (int e = tid; e <= M2; e += NT) {
           const double rho = sqrt(dr * dr + c * c + 4.0 * r * rt * S.s2tab[e]);
           double f0, f1, f2v;
-          smooth_factors(k * rho, &f0, &f1, &f2v);
+          smooth_factors(k * rho, ptab, &f0, &f1, &f2v);
           const ff a = ff_from_double(f0), b = ff_from_double(f1), cc = ff_from_double(f2v);
           S.fs[0][e] = make_float2(a.hi, a.lo);
           S.fs[1][e] = make_float2(b.hi, b.lo);
@@ -874,7 +896,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       }
       double kre, kim;
       const qd4 ys = x64[node0 + e];
-      smooth_kernel(xt, ys, n64[node0 + e], k, eta, &kre, &kim);
+      smooth_kernel(xt, ys, n64[node0 + e], k, eta, ptab, &kre, &kim);
       row[e].x -= kre * ys.w;
       row[e].y -= kim * ys.w;
     }
@@ -888,7 +910,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
     if (abs(i - p) <= 1) continue;
     const long long src = B.offset + e;
     double kre, kim;
-    smooth_kernel(xt, x64[src], n64[src], k, eta, &kre, &kim);
+    smooth_kernel(xt, x64[src], n64[src], k, eta, ptab, &kre, &kim);
     const double w = x64[src].w;
     row[e] = make_double2(kre * w, kim * w);
   }
@@ -915,6 +937,16 @@ int build_tables(qams_ctx* c, double r_extra, std::vector<AsmBody>& ab, std::vec
   std::vector<int> rule_off(64, -1);
   ab.assign(nb, AsmBody{});
   rules.clear();
+  // Miller coefficients alpha_n = 4(n-1)/(2n-3), beta_n = (2n-1)/(2n-3), n < MILLER_MAX
+  for (int n = 0; n < MILLER_MAX; ++n) {
+    rules.push_back(n >= 2 ? 4.0 * (n - 1) / (2.0 * n - 3.0) : 0.0);
+    rules.push_back(n >= 2 ? (2.0 * n - 1.0) / (2.0 * n - 3.0) : 0.0);
+  }
+  // table of the accurate-table sincos (phase.cuh), 16-byte aligned (offset 2 MILLER_MAX doubles)
+  for (int j = 0; j < PH_N; ++j) {
+    rules.push_back(std::cos(2.0 * M_PI * j / PH_N));
+    rules.push_back(std::sin(2.0 * M_PI * j / PH_N));
+  }
   long long blk = 0, rows = 0;
   int max_nb = 0, pstride = 0;
   for (int b = 0; b < nb; ++b) {

@@ -152,7 +152,7 @@ def test_workload_size_lattice_against_direct_sum():
     4 RHS): FP32 and float-float lattice applies against the direct ones."""
     import paper_2606_31380_b300 as q
     sc = scenes.lattice_of_workload(3)
-    ctx = lattice_ctx(sc, min_gap=0.5)
+    ctx = lattice_ctx(sc, min_gap=0.4)   # bounding balls 0.5 apart
     sigma = scenes.rhs_seeded(ctx.N, 4, 14)
     ctx.set_option(q.OPT_LATTICE, 0)
     d32 = gpu_pairsum(ctx, sigma, q.PREC_FP32)

@@ -233,10 +233,12 @@ __global__ void __launch_bounds__(FP_THREADS) freq_product_kernel(const T2* __re
     F ar[RC], ai[RC];
 #pragma unroll
     for (int r = 0; r < RC; ++r) ar[r] = ai[r] = F(0);
+    bool pairs = false;
     if constexpr (sizeof(T2) == sizeof(float2)) {
+      pairs = n >= 256;  // long complex64 rows: two entries (16 bytes) per lane and load
       // n is even (an even number of azimuths), so rows are 16-byte aligned pairs
       const float4* a = reinterpret_cast<const float4*>(A + (f * n + i) * n);
-      const int n2 = n >> 1;
+      const int n2 = pairs ? n >> 1 : 0;
       for (int j0 = lane; j0 < n2; j0 += 32 * U) {
         float4 v[U];
 #pragma unroll
@@ -253,7 +255,8 @@ __global__ void __launch_bounds__(FP_THREADS) freq_product_kernel(const T2* __re
           }
         }
       }
-    } else {
+    }
+    if (!pairs) {
       const T2* a = A + (f * n + i) * n;
       for (int j0 = lane; j0 < n; j0 += 32 * U) {
         T2 v[U];

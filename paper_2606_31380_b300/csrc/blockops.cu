@@ -24,12 +24,15 @@ struct Acc<float2> {
   using R = float;
 };
 
-// One warp per row g: y[g][r0+r] (+)= sum_col A_b[t][col] x[off+col][r0+r]
+// One warp per row g: y[g][r0+r] (+)= sum_col A_b[t][col] x[off+col][r0+r],
+// U block entries in flight per lane (the row streams from HBM; x is re-read
+// from L1/L2 by every row of the body).
 template <typename T2, int RC>
 __global__ void block_apply_kernel(const T2* __restrict__ blocks, const long long* __restrict__ blk_off,
                                    const long long* __restrict__ boff, int nb, long long N,
                                    const T2* __restrict__ x, T2* __restrict__ y, int R, int r0, int accumulate) {
   using F = typename Acc<T2>::R;
+  constexpr int U = RC >= 8 ? 2 : 4;
   const long long g = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (g >= N) return;
@@ -44,14 +47,28 @@ __global__ void block_apply_kernel(const T2* __restrict__ blocks, const long lon
   F ar[RC], ai[RC];
 #pragma unroll
   for (int r = 0; r < RC; ++r) ar[r] = ai[r] = F(0);
-  for (int col = lane; col < n; col += 32) {
-    const T2 a = row[col];
-    const T2* xv = x + (off + col) * R + r0;
+  for (int c0 = lane; c0 < n; c0 += 32 * U) {
+    T2 v[U];
 #pragma unroll
-    for (int r = 0; r < RC; ++r) {
-      const T2 v = xv[r];
-      ar[r] += a.x * v.x - a.y * v.y;
-      ai[r] += a.x * v.y + a.y * v.x;
+    for (int u = 0; u < U; ++u) {
+      if (c0 + 32 * u < n) {
+        v[u] = row[c0 + 32 * u];
+      } else {
+        v[u].x = F(0);
+        v[u].y = F(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int col = c0 + 32 * u;
+      if (col >= n) break;
+      const T2* xv = x + (off + col) * R + r0;
+#pragma unroll
+      for (int r = 0; r < RC; ++r) {
+        const T2 w = xv[r];
+        ar[r] += v[u].x * w.x - v[u].y * w.y;
+        ai[r] += v[u].x * w.y + v[u].y * w.x;
+      }
     }
   }
 #pragma unroll

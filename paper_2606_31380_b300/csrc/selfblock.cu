@@ -42,7 +42,7 @@
 namespace {
 
 constexpr int NT = 128;      // threads per CTA
-constexpr int BATCH = 16;    // outer nodes whose recursions run together (warp 0)
+constexpr int BATCH = 32;    // most outer nodes whose recursions run together (lanes of warp 0)
 constexpr int MAXP = 96;     // highest static mode N + n1 + 1
 constexpr int MAXM2 = 72;    // M/2 + 1 samples of the smooth factors
 constexpr int MAXN1 = 64;    // highest smooth-factor mode + 2 (k r_max up to ~35)
@@ -56,6 +56,7 @@ constexpr int MAXE = (MAXORD * 2 * MAXN + NT - 1) / NT;  // panel entries per th
 // end plus a graded innermost panel; nodes are generated from these
 // descriptors when a batch needs them.
 struct alignas(16) RowShared {
+  double rowc[8];               // row constants: cos, sin(theta_t); sin, cos(s_t); u_t, rho(u_t); r_t
   double pc_h0[4], pc_L[4];     // piece start (offset from s_t) and signed length
   int pc_K[4], pc_panel[4], pc_self[4], pc_end[4];  // levels, panel, u^6-graded innermost, cumulative node count
   int npc, nq;
@@ -108,16 +109,6 @@ __device__ __forceinline__ double rho_prof(const AsmBody& B, double u) {
     double sn, cs;
     sincospi(2.0 * m * u, &sn, &cs);
     s += B.a[m - 1] * cs + B.b[m - 1] * sn;
-  }
-  return B.base * s;
-}
-
-__device__ __forceinline__ double drho_prof(const AsmBody& B, double u) {
-  double s = 0.0;
-  for (int m = 1; m <= B.n_modes; ++m) {
-    double sn, cs;
-    sincospi(2.0 * m * u, &sn, &cs);
-    s += 2.0 * M_PI * m * (-B.a[m - 1] * sn + B.b[m - 1] * cs);
   }
   return B.base * s;
 }
@@ -205,25 +196,18 @@ __device__ __forceinline__ void series_at(const double* T, int nt, double s, dou
 
 __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, double s_t, double th_t, double h,
                           int P, int Nhalf, const double* __restrict__ inv_odd, double* q, double* dq, double* sc,
-                          const double* off) {
+                          const double* off, const double* rowc) {
   const double s = s_t + h;
   const double sh = sin(0.5 * h);
   const double mid = s_t + 0.5 * h;
   double r, rt, c, dr, alpha, a0, a1, b0, b1, b2, ca, sa;
-  double st, ct;
-  sincos(th_t, &st, &ct);
+  const double ct = rowc[0], st = rowc[1];
   if (B.kind == 1) {
     const int nt = B.n_terms;
     const double* T = tab + B.ser;
     double f[4], df[4], drop[4];
     for (int qq = 0; qq < 4; ++qq) series_at(T + 3 * nt * qq, nt, s, mid, h, &f[qq], &df[qq], &drop[qq]);
-    double r_t = 0.0;
-    for (int j = 0; j < nt; ++j) {
-      const double* t = T + 3 * (3 * nt + j);
-      double sn, cs;
-      sincos(t[0] * s_t, &sn, &cs);
-      r_t += t[1] * cs + t[2] * sn;
-    }
+    const double r_t = rowc[6];
     r = f[3];
     c = drop[2];
     const double dx = drop[0], dy = drop[1];
@@ -251,29 +235,49 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
     b1 = -r * df[0];
     b2 = -r * df[1];
   } else {
-    const double u_t = 0.5 * (1.0 + sin(s_t));
-    const double u = 0.5 * (1.0 + sin(s));
-    const double du = cos(mid) * sh;
-    double drho = 0.0;
+    const double u_t = rowc[4], rho_t = rowc[5], r_t = rowc[6];
+    double sin_s, cos_s, sin_mid, cos_mid;
+    sincos(s, &sin_s, &cos_s);
+    sincos(mid, &sin_mid, &cos_mid);
+    const double u = 0.5 * (1.0 + sin_s);
+    const double du = cos_mid * sh;  // u - u_t
+    // profile at u and its u-derivative, and rho(u) - rho(u_t) by sum-to-product,
+    //   cos 2pi m u - cos 2pi m u_t = -2 sin(pi m (u + u_t)) sin(pi m du),
+    //   sin 2pi m u - sin 2pi m u_t =  2 cos(pi m (u + u_t)) sin(pi m du),
+    // with the multiples of each angle by the angle-addition recurrence (m <= 8)
+    double s1, c1, sA, cA, sD, cD;
+    sincospi(2.0 * u, &s1, &c1);
+    sincospi(u + u_t, &sA, &cA);
+    sincospi(du, &sD, &cD);
+    double cm = c1, sm = s1, cAm = cA, sAm = sA, cDm = cD, sDm = sD;
+    double prof = 1.0, dprof = 0.0, drho = 0.0;
     for (int m = 1; m <= B.n_modes; ++m) {
-      double s1, c1;
-      sincospi(m * (u + u_t), &s1, &c1);
-      const double s2 = sinpi(m * du);
-      drho += -2.0 * B.a[m - 1] * s1 * s2 + 2.0 * B.b[m - 1] * c1 * s2;
+      const double am = B.a[m - 1], bm = B.b[m - 1];
+      prof += am * cm + bm * sm;
+      dprof += 2.0 * M_PI * m * (bm * cm - am * sm);
+      drho += 2.0 * sDm * (bm * cAm - am * sAm);
+      double t = cm * c1 - sm * s1;
+      sm = sm * c1 + cm * s1;
+      cm = t;
+      t = cAm * cA - sAm * sA;
+      sAm = sAm * cA + cAm * sA;
+      cAm = t;
+      t = cDm * cD - sDm * sD;
+      sDm = sDm * cD + cDm * sD;
+      cDm = t;
     }
     drho *= B.base;
-    const double rho_t = rho_prof(B, u_t);
-    const double r_t = rho_t * cos(s_t);
-    const double rho_s = rho_prof(B, u);
-    r = rho_s * cos(s);
-    const double dr_t = drho * cos(s) + rho_t * (-2.0 * sin(mid) * sh);
-    const double Delta = -B.L * cos(mid) * sh;
+    const double rho_s = B.base * prof;
+    r = rho_s * cos_s;
+    const double dr_t = drho * cos_s + rho_t * (-2.0 * sin_mid * sh);
+    const double Delta = -B.L * cos_mid * sh;
     const double kd = B.kappa * Delta;
-    const double sinc_h = fabs(kd) > 1e-8 ? sin(0.5 * kd) / (0.5 * kd) : 1.0;
-    const double sinc_f = fabs(kd) > 1e-8 ? sin(kd) / kd : 1.0;
+    double sh2, ch2;
+    sincos(0.5 * kd, &sh2, &ch2);
+    const double skd = 2.0 * sh2 * ch2, ckd = 1.0 - 2.0 * sh2 * sh2;
+    const double sinc_h = fabs(kd) > 1e-8 ? sh2 / (0.5 * kd) : 1.0;
+    const double sinc_f = fabs(kd) > 1e-8 ? skd / kd : 1.0;
     const double omc = 0.5 * B.kappa * Delta * Delta * sinc_h * sinc_h;
-    double skd, ckd;
-    sincos(kd, &skd, &ckd);
     const double a = omc + r_t * ct * ckd;
     const double b = r_t * st;
     c = Delta * sinc_f - r_t * ct * skd;
@@ -296,8 +300,8 @@ __device__ void ring_node(const AsmBody& B, const double* __restrict__ tab, doub
     alpha = atan2(bo, ao);
     ca = ao / rt;
     sa = bo / rt;
-    const double dl = 0.5 * B.L * cos(s);                                    // l'(s)
-    const double rp = drho_prof(B, u) * 0.5 * cos(s) * cos(s) - rho_s * sin(s);  // r'(s)
+    const double dl = 0.5 * B.L * cos_s;                                       // l'(s)
+    const double rp = B.base * dprof * 0.5 * cos_s * cos_s - rho_s * sin_s;    // r'(s)
     a0 = r * dl;
     a1 = -B.kappa * r * r * dl;
     b0 = -r * rp;
@@ -457,16 +461,17 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
                                                        const double* __restrict__ jac, double k, double eta,
                                                        long long row0, double2* __restrict__ blocks,
                                                        unsigned long long* __restrict__ counts, int pstride,
+                                                       int batch,
                                                        const NearTarget* __restrict__ near) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   RowShared& S = *reinterpret_cast<RowShared*>(smem_raw);
-  // Q_{m-1/2} and dQ/dchi of the batch, [BATCH][pstride] each (pstride >= P + 1, even),
+  // Q_{m-1/2} and dQ/dchi of the batch, [batch][pstride] each (pstride >= P + 1, even),
   // then the modal-domain accumulators of the current panel, [order][2N] complex each
   // for the double layer and the single layer (RowShared's size is a multiple of 16,
   // so every array stays 16-byte aligned)
   double* bq = reinterpret_cast<double*>(smem_raw + sizeof(RowShared));
-  double* bdq = bq + BATCH * pstride;
-  float4* accD = reinterpret_cast<float4*>(bdq + BATCH * pstride);
+  double* bdq = bq + batch * pstride;
+  float4* accD = reinterpret_cast<float4*>(bdq + batch * pstride);
 
   // rows of the assembled bodies (one per class of congruent bodies), back to back;
   // or, with `near`, one off-surface target per CTA (the near-field rows)
@@ -562,6 +567,33 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
     }
     S.npc = npc;
     S.nq = nq;
+    // row constants of the ring-target geometry
+    double sth, cth;
+    sincos(th_t, &sth, &cth);
+    S.rowc[0] = cth;
+    S.rowc[1] = sth;
+    if (B.kind == 1) {
+      const int nt = B.n_terms;
+      const double* T = rules + B.ser;
+      double r_t = 0.0;
+      for (int j = 0; j < nt; ++j) {
+        const double* tt = T + 3 * (3 * nt + j);
+        double sn, cs;
+        sincos(tt[0] * s_t, &sn, &cs);
+        r_t += tt[1] * cs + tt[2] * sn;
+      }
+      S.rowc[6] = r_t;
+    } else {
+      double sst, cst;
+      sincos(s_t, &sst, &cst);
+      const double u_t = 0.5 * (1.0 + sst);
+      const double rho_t = rho_prof(B, u_t);
+      S.rowc[2] = sst;
+      S.rowc[3] = cst;
+      S.rowc[4] = u_t;
+      S.rowc[5] = rho_t;
+      S.rowc[6] = rho_t * cst;
+    }
   }
   // row tables
   for (int q = tid; q <= M2; q += NT) {
@@ -581,8 +613,8 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
   __syncthreads();
   const int nq = S.nq;
 
-  for (int b0 = 0; b0 < nq; b0 += BATCH) {
-    const int nbatch = min(BATCH, nq - b0);
+  for (int b0 = 0; b0 < nq; b0 += batch) {
+    const int nbatch = min(batch, nq - b0);
     if (tid < nbatch) {
       double hq, wq;
       int pq, fq;
@@ -591,7 +623,7 @@ __global__ void __launch_bounds__(NT, 3) selfblock_kernel(const AsmBody* __restr
       S.bp[tid] = pq;
       S.bflush[tid] = fq;
       ring_node(B, rules, s_t, th_t, hq, P, N, S.inv_odd, bq + tid * pstride, bdq + tid * pstride, S.bs[tid],
-                toff);
+                toff, S.rowc);
     }
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
@@ -922,8 +954,14 @@ static_assert(sizeof(RowShared) % 16 == 0, "double2 accumulators follow RowShare
 
 // Dynamic shared memory of one CTA: RowShared, Q and dQ of a batch, two panel
 // accumulators of float-float complex entries.
-size_t qams_selfblock_smem(int max_per_panel, int pstride) {
-  return sizeof(RowShared) + 2 * sizeof(double) * BATCH * (size_t)pstride + 2 * sizeof(float4) * (size_t)max_per_panel;
+size_t qams_selfblock_smem(int max_per_panel, int pstride, int batch) {
+  return sizeof(RowShared) + 2 * sizeof(double) * batch * (size_t)pstride + 2 * sizeof(float4) * (size_t)max_per_panel;
+}
+
+// Outer nodes per batch: all 32 lanes of warp 0 when three CTAs still fit on an SM
+// (228 KB of shared memory, 1 KB reserved per CTA), else 16.
+int qams_selfblock_batch(int max_per_panel, int pstride) {
+  return 3 * (qams_selfblock_smem(max_per_panel, pstride, 32) + 1024) <= 228 * 1024 ? 32 : 16;
 }
 
 namespace {
@@ -1052,13 +1090,14 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
   QAMS_CUDA(cudaMemcpy(d_rules.p, rules.data(), sizeof(double) * rules.size(), cudaMemcpyHostToDevice));
   if ((rc = qams_dev_alloc(c, &d_counts, 2 * sizeof(unsigned long long)))) return rc;
   QAMS_CUDA(cudaMemsetAsync(d_counts.p, 0, 2 * sizeof(unsigned long long), st));
-  const size_t smem = qams_selfblock_smem(max_nb, pstride);
+  const int batch = qams_selfblock_batch(max_nb, pstride);
+  const size_t smem = qams_selfblock_smem(max_nb, pstride, batch);
   // The attribute is process-wide: requests served concurrently must not lower it under
   // one another, so it is always set to the kernel's largest possible launch size.
   static_assert(sizeof(RowShared) + 2 * sizeof(double) * BATCH * (MAXP + 2) +
                         2 * sizeof(float4) * MAXORD * 2 * MAXN <= 227 * 1024,
                 "largest self-block launch exceeds the shared memory of a CTA");
-  const int smem_max = (int)qams_selfblock_smem(MAXORD * 2 * MAXN, MAXP + 2);
+  const int smem_max = (int)qams_selfblock_smem(MAXORD * 2 * MAXN, MAXP + 2, BATCH);
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   const long long chunk = 1 << 20;
@@ -1069,7 +1108,7 @@ int qams_assemble_launch(qams_ctx* c, cudaStream_t st) {
                                                     (const qd4*)c->x64.p, (const qd4*)c->n64.p,
                                                     (const double*)c->jac64.p, c->k, c->eta, r0,
                                                     (double2*)c->blocks64.p, (unsigned long long*)d_counts.p,
-                                                    pstride, nullptr); qams_count_launch();
+                                                    pstride, batch, nullptr); qams_count_launch();
     qams_prof_end(c, QAMS_PROF_ASSEMBLY, st, pe);
     QAMS_CUDA(cudaGetLastError());
   }
@@ -1104,8 +1143,9 @@ int qams_near_rows_launch(qams_ctx* c, const NearTarget* targets, long long n, d
   }
   QAMS_CUDA(cudaMemcpy(d_bodies.p, ab.data(), sizeof(AsmBody) * nb, cudaMemcpyHostToDevice));
   QAMS_CUDA(cudaMemcpy(d_rules.p, rules.data(), sizeof(double) * rules.size(), cudaMemcpyHostToDevice));
-  const size_t smem = qams_selfblock_smem(max_nb, pstride);
-  const int smem_max = (int)qams_selfblock_smem(MAXORD * 2 * MAXN, MAXP + 2);
+  const int batch = qams_selfblock_batch(max_nb, pstride);
+  const size_t smem = qams_selfblock_smem(max_nb, pstride, batch);
+  const int smem_max = (int)qams_selfblock_smem(MAXORD * 2 * MAXN, MAXP + 2, BATCH);
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max));
   QAMS_CUDA(cudaFuncSetAttribute(selfblock_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   const long long chunk = 1 << 20;
@@ -1114,7 +1154,7 @@ int qams_near_rows_launch(qams_ctx* c, const NearTarget* targets, long long n, d
     selfblock_kernel<<<(unsigned)m, NT, smem, st>>>((const AsmBody*)d_bodies.p, nb, (const double*)d_rules.p,
                                                     (const qd4*)c->x64.p, (const qd4*)c->n64.p,
                                                     (const double*)c->jac64.p, c->k, c->eta, r0, rows, nullptr,
-                                                    pstride, targets);
+                                                    pstride, batch, targets);
     qams_count_launch();
     QAMS_CUDA(cudaGetLastError());
   }

@@ -20,23 +20,30 @@ namespace {
 
 constexpr int MAXR = 16;
 
-// one warp per (point, body) pair: u[m][r0 + r] += row . mu_b[:, r0 + r]
-__global__ void near_apply_kernel(const NearTarget* __restrict__ T, long long n, const double2* __restrict__ rows,
-                                  const double2* __restrict__ mu, int R, int r0, int rc, double2* u) {
+// one warp per corrected point: its (point, body) pairs T[beg[k]..beg[k+1]) in
+// order, u[m][r0 + r] += sum over the pairs of row . mu_b[:, r0 + r]
+// (one writer per point: the sum does not depend on scheduling)
+__global__ void near_apply_kernel(const NearTarget* __restrict__ T, const int* __restrict__ beg, int npts,
+                                  const double2* __restrict__ rows, const double2* __restrict__ mu, int R, int r0,
+                                  int rc, double2* u) {
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= n) return;
-  const NearTarget t = T[w];
-  const double2* row = rows + t.row;
+  if (w >= npts) return;
   double ar[MAXR], ai[MAXR];
   for (int r = 0; r < rc; ++r) ar[r] = ai[r] = 0.0;
-  for (int col = lane; col < t.n; col += 32) {
-    const double2 a = row[col];
-    const double2* mv = mu + (t.node0 + col) * R + r0;
-    for (int r = 0; r < rc; ++r) {
-      const double2 v = mv[r];
-      ar[r] += a.x * v.x - a.y * v.y;
-      ai[r] += a.x * v.y + a.y * v.x;
+  int m = 0;
+  for (int k = beg[w]; k < beg[w + 1]; ++k) {
+    const NearTarget t = T[k];
+    m = t.m;
+    const double2* row = rows + t.row;
+    for (int col = lane; col < t.n; col += 32) {
+      const double2 a = row[col];
+      const double2* mv = mu + (t.node0 + col) * R + r0;
+      for (int r = 0; r < rc; ++r) {
+        const double2 v = mv[r];
+        ar[r] += a.x * v.x - a.y * v.y;
+        ai[r] += a.x * v.y + a.y * v.x;
+      }
     }
   }
   for (int r = 0; r < rc; ++r) {
@@ -45,9 +52,9 @@ __global__ void near_apply_kernel(const NearTarget* __restrict__ T, long long n,
       ai[r] += __shfl_xor_sync(0xffffffffu, ai[r], o);
     }
     if (lane == 0) {
-      double2* dst = u + (long long)t.m * R + r0 + r;
-      atomicAdd(&dst->x, ar[r]);
-      atomicAdd(&dst->y, ai[r]);
+      double2* dst = u + (long long)m * R + r0 + r;
+      dst->x += ar[r];
+      dst->y += ai[r];
     }
   }
 }
@@ -112,27 +119,38 @@ int qams_near_correction(qams_ctx* c, int R, const void* mu, int M, const double
   const long long cap = std::max<long long>(1LL << 26, tg.front().n);
   int rc = QAMS_OK;
   for (size_t i0 = 0; i0 < tg.size() && !rc;) {
+    // a chunk ends on a point boundary (pairs are generated point by point)
     size_t i1 = i0;
     const long long base = tg[i0].row;
     while (i1 < tg.size() && tg[i1].row + tg[i1].n - base <= cap) ++i1;
     if (i1 == i0) i1 = i0 + 1;
+    while (i1 < tg.size() && i1 > i0 + 1 && tg[i1].m == tg[i1 - 1].m) --i1;
+    while (i1 < tg.size() && tg[i1].m == tg[i1 - 1].m) ++i1;
     std::vector<NearTarget> part(tg.begin() + i0, tg.begin() + i1);
+    std::vector<int> beg{0};
+    for (size_t k = 1; k < part.size(); ++k)
+      if (part[k].m != part[k - 1].m) beg.push_back((int)k);
+    beg.push_back((int)part.size());
+    const int npts = (int)beg.size() - 1;
     for (NearTarget& t : part) t.row -= base;
     const long long ent = part.back().row + part.back().n;
-    DeviceBuf d_t, d_rows;
+    DeviceBuf d_t, d_rows, d_beg;
     rc = qams_dev_alloc(c, &d_t, sizeof(NearTarget) * part.size());
+    if (!rc) rc = qams_dev_alloc(c, &d_beg, sizeof(int) * beg.size());
     if (!rc) rc = qams_dev_alloc(c, &d_rows, sizeof(double2) * (size_t)ent);
-    if (!rc && cudaMemcpyAsync(d_t.p, part.data(), sizeof(NearTarget) * part.size(), cudaMemcpyHostToDevice, st) !=
-                   cudaSuccess)
+    if (!rc && (cudaMemcpyAsync(d_t.p, part.data(), sizeof(NearTarget) * part.size(), cudaMemcpyHostToDevice, st) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(d_beg.p, beg.data(), sizeof(int) * beg.size(), cudaMemcpyHostToDevice, st) !=
+                    cudaSuccess))
       rc = QAMS_ECUDA;
     if (!rc) rc = qams_near_rows_launch(c, (const NearTarget*)d_t.p, (long long)part.size(), r_extra,
                                         (double2*)d_rows.p, st);
     if (!rc) {
-      const long long threads = (long long)part.size() * 32;
+      const long long threads = (long long)npts * 32;
       for (int r0 = 0; r0 < R; r0 += MAXR) {
         const int cnt = std::min(MAXR, R - r0);
         near_apply_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-            (const NearTarget*)d_t.p, (long long)part.size(), (const double2*)d_rows.p, (const double2*)mu, R, r0,
+            (const NearTarget*)d_t.p, (const int*)d_beg.p, npts, (const double2*)d_rows.p, (const double2*)mu, R, r0,
             cnt, (double2*)u);
         qams_count_launch();
       }
@@ -140,6 +158,7 @@ int qams_near_correction(qams_ctx* c, int R, const void* mu, int M, const double
       if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = QAMS_ECUDA;
     }
     qams_dev_free(c, &d_t);
+    qams_dev_free(c, &d_beg);
     qams_dev_free(c, &d_rows);
     i0 = i1;
   }

@@ -344,6 +344,8 @@ def run_lattice(q, torch, sc, steps, warmup, tol, local_rank):
     w = dict(recs=recs, elapsed=elapsed, applies=applies, pair_evals=sum(a * pairs * R for a in applies))
     out = summary(w, steps, 1)
     out["workload"] = sc.name
+    out["value_note"] = ("equivalent rate: the N^2 - sum n_b^2 pair interactions of each apply, applied through "
+                         "the circulant embedding of the displacement blocks")
     out["lattice_pairsum_ms_per_apply"] = ms_lat / max(nlat, 1)
     # the per-frequency products stream the transformed blocks: (2P-1)(2Q-1)(2R-1) n^2 entries
     F = 1

@@ -23,6 +23,9 @@ Modules, each following the paper's steps in its order and notation:
 * ``operator``  -- the inter-body smooth rule (Eq. multi2part), the full
                    operator apply, the incident field and the far field.
 * ``solve``     -- dense LU and restarted GMRES (Sec. 6, solver description).
+* ``nearfield`` -- the layer potential of the interpolated density at
+                   off-surface points as a plain adaptive 2-D integral (the
+                   field near a surface, Sec. 6).
 
 Parity status of every function is stated in its module header.
 """

@@ -130,6 +130,16 @@ __global__ void add_kernel(double2* __restrict__ x, const double2* __restrict__ 
   }
 }
 
+// s[r] = 1 / sqrt(max(0, nsq[r].x)) (0 for a zero or NaN norm; the host reads the
+// norms back and rejects a non-finite one)
+__global__ void inv_norm_kernel(const double2* __restrict__ nsq, double2* __restrict__ s, int R) {
+  const int r = threadIdx.x;
+  if (r >= R) return;
+  const double v = nsq[r].x;
+  const double hn = isnan(v) ? v : sqrt(fmax(0.0, v));
+  s[r] = make_double2(hn > 0.0 ? 1.0 / hn : 0.0, 0.0);
+}
+
 inline unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
 
 struct Solver {
@@ -137,7 +147,7 @@ struct Solver {
   int R, m;
   long long N;
   cudaStream_t st;
-  DeviceBuf V, w, partial, hbuf, t32a, t32b, t32c, t64;
+  DeviceBuf V, w, partial, hbuf, hstep, t32a, t32b, t32c, t64;
   std::vector<double2> hhost;
   bool prec = false;  // right block-Jacobi preconditioning: the operator is A P^{-1}
 
@@ -147,15 +157,16 @@ struct Solver {
     if ((rc = qams_dev_alloc(c, &w, sizeof(double2) * (size_t)N * R))) return rc;
     if ((rc = qams_dev_alloc(c, &partial, sizeof(double2) * (size_t)DOT_BLOCKS * (m + 1) * R))) return rc;
     if ((rc = qams_dev_alloc(c, &hbuf, sizeof(double2) * (size_t)(m + 1) * R))) return rc;
+    if ((rc = qams_dev_alloc(c, &hstep, sizeof(double2) * (size_t)(2 * (m + 1) + 2) * R))) return rc;
     if ((rc = qams_dev_alloc(c, &t32a, sizeof(float2) * (size_t)N * R))) return rc;
     if ((rc = qams_dev_alloc(c, &t32b, sizeof(float2) * (size_t)N * R))) return rc;
     if ((rc = qams_dev_alloc(c, &t32c, sizeof(float2) * (size_t)N * R))) return rc;
     if ((rc = qams_dev_alloc(c, &t64, sizeof(double2) * (size_t)N * R))) return rc;
-    hhost.resize((size_t)(m + 1) * R);
+    hhost.resize((size_t)(2 * (m + 1) + 2) * R);
     return QAMS_OK;
   }
   void release() {
-    for (DeviceBuf* b : {&V, &w, &partial, &hbuf, &t32a, &t32b, &t32c, &t64}) qams_dev_free(c, b);
+    for (DeviceBuf* b : {&V, &w, &partial, &hbuf, &hstep, &t32a, &t32b, &t32c, &t64}) qams_dev_free(c, b);
   }
   double2* Vi(int i) { return (double2*)V.p + (size_t)i * N * R; }
 
@@ -219,6 +230,14 @@ struct Solver {
     QAMS_CUDA(cudaStreamSynchronize(st));
     return QAMS_OK;
   }
+  // out_dev[i][r] = <V_i, v> for i < ni, left on the device
+  int dots_dev(const double2* Vbase, int ni, const double2* v, double2* out_dev) {
+    multidot_kernel<<<dim3(DOT_BLOCKS, ni), 256, 0, st>>>(Vbase, N * R, v, N, R, (double2*)partial.p); qams_count_launch();
+    reduce_partial_kernel<<<(ni * R + 127) / 128, 128, 0, st>>>((const double2*)partial.p, DOT_BLOCKS, ni, R,
+                                                               out_dev); qams_count_launch();
+    QAMS_CUDA(cudaGetLastError());
+    return QAMS_OK;
+  }
   int norms(const double2* v, std::vector<double>& out) {
     int rc = dots(v, 1, v);
     if (rc) return rc;
@@ -268,22 +287,36 @@ struct Solver {
       bool conv = false;
       for (; j < m && it < maxit; ++j) {
         if ((rc = op(Vi(j), (double2*)w.p, precision))) return rc;
+        // classical Gram-Schmidt twice, the norm and the new basis vector on the device;
+        // one read-back per step: [pass 0 (j+1) R][pass 1 (j+1) R][|w|^2 R]
+        double2* h0 = (double2*)hstep.p;
+        double2* h1 = h0 + (size_t)(j + 1) * R;
+        double2* nsq = h1 + (size_t)(j + 1) * R;
+        double2* scl = nsq + R;
         for (int pass = 0; pass < 2; ++pass) {
-          if ((rc = dots(Vi(0), j + 1, (const double2*)w.p))) return rc;
+          double2* hp = pass == 0 ? h0 : h1;
+          if ((rc = dots_dev(Vi(0), j + 1, (const double2*)w.p, hp))) return rc;
+          basis_combine_kernel<<<nblk(n), 256, 0, st>>>(Vi(0), N * R, j + 1, hp, (double2*)w.p, N, R, -1.0); qams_count_launch();
+        }
+        if ((rc = dots_dev((const double2*)w.p, 1, (const double2*)w.p, nsq))) return rc;
+        inv_norm_kernel<<<1, 32, 0, st>>>(nsq, scl, R); qams_count_launch();
+        scale_cols_kernel<<<nblk(n), 256, 0, st>>>((const double2*)w.p, scl, Vi(j + 1), N, R); qams_count_launch();
+        QAMS_CUDA(cudaGetLastError());
+        const size_t nback = (size_t)(2 * (j + 1) + 1) * R;
+        QAMS_CUDA(cudaMemcpyAsync(hhost.data(), h0, sizeof(double2) * nback, cudaMemcpyDeviceToHost, st));
+        QAMS_CUDA(cudaStreamSynchronize(st));
+        for (int pass = 0; pass < 2; ++pass)
           for (int i = 0; i <= j; ++i)
-            for (int r = 0; r < R; ++r) H[((size_t)i * m + j) * R + r] += cd(hhost[i * R + r].x, hhost[i * R + r].y);
-          basis_combine_kernel<<<nblk(n), 256, 0, st>>>(Vi(0), N * R, j + 1, (const double2*)hbuf.p,
-                                                        (double2*)w.p, N, R, -1.0); qams_count_launch();
-        }
-        std::vector<double> hn;
-        if ((rc = norms((const double2*)w.p, hn))) return rc;
+            for (int r = 0; r < R; ++r) {
+              const double2 v = hhost[(size_t)(pass * (j + 1) + i) * R + r];
+              H[((size_t)i * m + j) * R + r] += cd(v.x, v.y);
+            }
         for (int r = 0; r < R; ++r) {
-          if (!std::isfinite(hn[r])) return QAMS_ENUMERIC;
-          H[((size_t)(j + 1) * m + j) * R + r] = hn[r];
-          sc[r] = make_double2(hn[r] > 0 ? 1.0 / hn[r] : 0.0, 0.0);
+          const double v = hhost[(size_t)2 * (j + 1) * R + r].x;
+          const double hn = std::isnan(v) ? v : std::sqrt(std::max(0.0, v));
+          if (!std::isfinite(hn)) return QAMS_ENUMERIC;
+          H[((size_t)(j + 1) * m + j) * R + r] = hn;
         }
-        QAMS_CUDA(cudaMemcpyAsync(hbuf.p, sc.data(), sizeof(double2) * R, cudaMemcpyHostToDevice, st));
-        scale_cols_kernel<<<nblk(n), 256, 0, st>>>((const double2*)w.p, (const double2*)hbuf.p, Vi(j + 1), N, R); qams_count_launch();
         // Givens rotations per column: G_i = [[c*, s*], [-s, c]]
         bool all = true;
         for (int r = 0; r < R; ++r) {

@@ -218,12 +218,13 @@ int qams_set_bodies(qams_ctx* ctx, int n_bodies, const qams_body_desc* bodies, d
  * their displacement d = (p_t - p_s, q_t - q_s, r_t - r_s) (the block
  * Toeplitz structure of Sec. 4).  qams_lattice_prepare (called by
  * qams_assemble) forms the (2 dims[0] - 1)(2 dims[1] - 1)(2 dims[2] - 1)
- * distinct blocks T(d)[i][j] = K(x~_i + d.A, y~_j) in FP64, embeds them in
- * a circulant of those periods and transforms them by the 3-D discrete
- * Fourier transform; from then on qams_pairsum (and so qams_apply and
- * qams_solve) computes the same sums as the direct pair sum by per-frequency
- * n x n products: complex64 blocks for QAMS_PREC_FP32, complex128 for
- * QAMS_PREC_FF and QAMS_PREC_FP64 (FP64 throughout; no phase split is
+ * distinct blocks T(d)[i][j] = K(x~_i + d.A, y~_j) (values in FP64), embeds
+ * them in a circulant of those periods and transforms them by the 3-D
+ * discrete Fourier transform (float-float sums, ~1e-14 relative); from then
+ * on qams_pairsum (and so qams_apply and qams_solve) computes the same sums
+ * as the direct pair sum by per-frequency n x n products: complex64 blocks
+ * and FP32 arithmetic for QAMS_PREC_FP32, complex128 blocks and FP64
+ * arithmetic for QAMS_PREC_FF and QAMS_PREC_FP64 (no phase split is
  * needed).  Library-owned device memory: (16 + 8) n^2 prod(2 dims - 1)
  * bytes of blocks plus two [prod(2 dims - 1)][n][R] complex workspaces
  * sized at the first apply.  A later qams_set_bodies ends the lattice mode.

@@ -134,6 +134,14 @@ def test_sixteen_bodies_full_size_residual_rows():
         row = self_block_rows_parallel(nodes[bi], [gidx - off[bi]], sc.k, sc.eta, workers=1)[0]
         Am[i] += row @ m[off[bi]:off[bi + 1]]
     assert np.max(np.abs(Am - bb[rows])) < 1e-9 * np.max(np.abs(bb))
+    # one row per body, every column: the GPU self-block part (its rows are checked against
+    # the oracle's elsewhere to 1e-12) plus the oracle's explicit pair sum
+    ys = torch.zeros_like(mu)
+    ctx.selfblock_apply(mu, ys, q.PREC_FP64)
+    rows_all = off[:-1] + (np.arange(len(sc.bodies)) * 37) % 512
+    Ap = op.pair_sum(nodes, w[:, None] * m, sc.k, sc.eta, targets=rows_all)
+    res_all = bb[rows_all] - ys.cpu().numpy()[rows_all] - Ap
+    assert np.max(np.abs(res_all)) < 1e-9 * np.max(np.abs(bb))
 
 
 def test_block_jacobi_preconditioner():

@@ -255,6 +255,15 @@ int qams_get_nodes(const qams_ctx* ctx, double* x_host, double* n_host, double* 
  * Errors: QAMS_EINVAL (the descriptor conditions of qams_set_bodies). */
 int qams_body_nodes(const qams_body_desc* body, double* x_host, double* n_host, double* w_host);
 
+/* The nearest surface point of one body to the world point x_host[3], as
+ * qams_field's near-field correction finds it (Gauss-Newton on (s, theta)
+ * from the nearest node): the surface parameters s_out in [-pi/2, pi/2]
+ * (kept 1e-7 inside the poles) and theta_out in [0, 2 pi), and the distance.
+ * Host only, no context or device.  Errors: QAMS_EINVAL (NULL pointers, the
+ * descriptor conditions of qams_set_bodies). */
+int qams_nearest_surface_point(const qams_body_desc* body, const double* x_host, double* s_out, double* theta_out,
+                               double* dist_out);
+
 /* Wavenumber k > 0 and combined-layer coupling eta (0 = pure double layer,
  * Eq. multi-double; 1 = the default of the Sec. 2 Remark). */
 int qams_set_wavenumber(qams_ctx* ctx, double k, double eta);

@@ -116,6 +116,7 @@ def load_library():
         "qams_set_lattice": (i, [vp, C.POINTER(BodyDesc), vp, vp, d]),
         "qams_lattice_prepare": (i, [vp, vp]),
         "qams_field_near_pairs": (i, [vp, C.POINTER(ll)]),
+        "qams_nearest_surface_point": (i, [vp, vp, C.POINTER(d), C.POINTER(d), C.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -430,6 +431,18 @@ def body_nodes(body):
     _check(lib.qams_body_nodes(C.cast(arr, C.c_void_p), x.ctypes.data_as(C.c_void_p),
                                nn.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)), "qams_body_nodes")
     return x, nn, w
+
+
+def nearest_surface_point(body, x):
+    """(s, theta, distance) of the nearest surface point of one body to the
+    world point x, as the near-field correction finds it -- no device needed."""
+    lib = load_library()
+    arr, keep = body_desc_array([body])
+    xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(3))
+    s, th, dist = C.c_double(), C.c_double(), C.c_double()
+    _check(lib.qams_nearest_surface_point(C.cast(arr, C.c_void_p), xx.ctypes.data_as(C.c_void_p), C.byref(s),
+                                          C.byref(th), C.byref(dist)), "qams_nearest_surface_point")
+    return s.value, th.value, dist.value
 
 
 def footprint(bodies, R: int, restart: int = 50) -> int:

@@ -294,9 +294,19 @@ void qams_nearest_point(const BodyHost& b, const double* hx_body, const double x
   double s = 0.5 * (b.breaks[p0] + b.breaks[p0 + 1]) + 0.5 * (b.breaks[p0 + 1] - b.breaks[p0]) * gx[l0];
   double th = 2.0 * M_PI * j0 / d.n_theta;
   const double smax = 0.5 * M_PI - 1e-7;
-  // Gauss-Newton on |x - y(s, th)|^2 with difference Jacobians (their error only slows
-  // the iteration; the fixed point is set by the exact residual)
-  for (int it = 0; it < 60; ++it) {
+  // Levenberg-Marquardt on f = |x - y(s, th)|^2 with difference Jacobians: a step is
+  // taken only if it lowers f (so the result is never farther than the nearest node,
+  // also where the surface curves on the scale of the distance, e.g. near a pole);
+  // the Jacobian's error only slows the iteration, the fixed point is set by f
+  auto dist2 = [&](double ss, double tt) {
+    double p[3], nn[3], jac;
+    sh.eval(ss, tt, p, nn, &jac);
+    double f = 0.0;
+    for (int q = 0; q < 3; ++q) f += (xl[q] - p[q]) * (xl[q] - p[q]);
+    return f;
+  };
+  double f = dist2(s, th), lam = 1e-3;
+  for (int it = 0; it < 100; ++it) {
     double p[3], nn[3], jac, pa[3], pb[3], dummy;
     const double hs = 1e-6, ht = 1e-6;
     sh.eval(s, th, p, nn, &jac);
@@ -308,28 +318,39 @@ void qams_nearest_point(const BodyHost& b, const double* hx_body, const double x
     sh.eval(s, th + ht, pa, nn, &dummy);
     sh.eval(s, th - ht, pb, nn, &dummy);
     for (int q = 0; q < 3; ++q) Jt[q] = (pa[q] - pb[q]) / (2.0 * ht);
-    double r[3];
-    for (int q = 0; q < 3; ++q) r[q] = xl[q] - p[q];
     double a11 = 0, a12 = 0, a22 = 0, g1 = 0, g2 = 0;
     for (int q = 0; q < 3; ++q) {
+      const double r = xl[q] - p[q];
       a11 += Js[q] * Js[q];
       a12 += Js[q] * Jt[q];
       a22 += Jt[q] * Jt[q];
-      g1 += Js[q] * r[q];
-      g2 += Jt[q] * r[q];
+      g1 += Js[q] * r;
+      g2 += Jt[q] * r;
     }
-    const double lam = 1e-12 * (a11 + a22);
-    a11 += lam;
-    a22 += lam;
-    const double det = a11 * a22 - a12 * a12;
-    if (!(det > 0.0)) break;
-    double ds = (a22 * g1 - a12 * g2) / det, dt = (a11 * g2 - a12 * g1) / det;
-    // keep steps inside a node spacing's order of magnitude
-    ds = std::max(-0.25, std::min(0.25, ds));
-    dt = std::max(-0.5, std::min(0.5, dt));
-    s = std::max(-smax, std::min(smax, s + ds));
-    th += dt;
-    if (std::fabs(ds) < 1e-13 && std::fabs(dt) < 1e-13) break;
+    bool moved = false;
+    for (int tries = 0; tries < 30 && !moved; ++tries) {
+      const double b11 = a11 * (1.0 + lam) + 1e-300, b22 = a22 * (1.0 + lam) + 1e-300;
+      const double det = b11 * b22 - a12 * a12;
+      if (!(det > 0.0)) {
+        lam *= 10.0;
+        continue;
+      }
+      const double ds = (b22 * g1 - a12 * g2) / det, dt = (b11 * g2 - a12 * g1) / det;
+      const double s2 = std::max(-smax, std::min(smax, s + ds)), t2 = th + dt;
+      const double f2 = dist2(s2, t2);
+      if (f2 < f) {
+        const bool small = std::fabs(s2 - s) < 1e-14 && std::fabs(t2 - th) < 1e-14;
+        s = s2;
+        th = t2;
+        f = f2;
+        lam = std::max(lam * 0.1, 1e-12);
+        moved = true;
+        if (small) it = 100;
+      } else {
+        lam *= 10.0;
+      }
+    }
+    if (!moved) break;
   }
   th = std::fmod(th, 2.0 * M_PI);
   if (th < 0) th += 2.0 * M_PI;
@@ -364,6 +385,21 @@ void qams_nearest_point(const BodyHost& b, const double* hx_body, const double x
   *s_out = s;
   *th_out = th;
   *panel_out = pan;
+}
+
+extern "C" int qams_nearest_surface_point(const qams_body_desc* desc, const double* x, double* s_out,
+                                          double* theta_out, double* dist_out) {
+  if (!desc || !x || !s_out || !theta_out || !dist_out) return QAMS_EINVAL;
+  BodyHost b;
+  const int rc = qams_copy_body(*desc, &b);
+  if (rc) return rc;
+  b.n = b.d.n_panels * b.d.order * b.d.n_theta;
+  std::vector<double> hx(3 * (size_t)b.n);
+  body_nodes_into(b, hx.data(), nullptr, nullptr, nullptr);
+  int panel;
+  double ds, v[3];
+  qams_nearest_point(b, hx.data(), x, s_out, theta_out, &panel, dist_out, &ds, v);
+  return QAMS_OK;
 }
 
 std::string qams_shape_key(const BodyCopy& bc) {

@@ -256,8 +256,9 @@ int qams_get_nodes(const qams_ctx* ctx, double* x_host, double* n_host, double* 
 int qams_body_nodes(const qams_body_desc* body, double* x_host, double* n_host, double* w_host);
 
 /* The nearest surface point of one body to the world point x_host[3], as
- * qams_field's near-field correction finds it (Gauss-Newton on (s, theta)
- * from the nearest node): the surface parameters s_out in [-pi/2, pi/2]
+ * qams_field's near-field correction finds it (Levenberg-Marquardt on
+ * (s, theta) from the nearest node, a step taken only when it brings the
+ * surface point closer): the surface parameters s_out in [-pi/2, pi/2]
  * (kept 1e-7 inside the poles) and theta_out in [0, 2 pi), and the distance.
  * Host only, no context or device.  Errors: QAMS_EINVAL (NULL pointers, the
  * descriptor conditions of qams_set_bodies). */
@@ -440,7 +441,7 @@ int qams_farfield(qams_ctx* ctx, int R, const void* mu_dev, int M, const double*
  * the self blocks' product integration (Sec. 3) taken at the off-surface
  * target: modal Green's functions of the source rings seen from x, the
  * outer integral graded toward the nearest surface point (found on the host
- * by Gauss-Newton from the nearest node).  The result is then the layer
+ * by Levenberg-Marquardt from the nearest node, qams_nearest_surface_point).  The result is then the layer
  * potential of the interpolated density on those panels, accurate at any
  * distance off the surface; points on a surface are not supported.  mu_dev
  * [N][R] and u_dev [M][R] are complex128.  Blocking on `stream`.

@@ -441,9 +441,10 @@ int qams_farfield(qams_ctx* ctx, int R, const void* mu_dev, int M, const double*
  * the self blocks' product integration (Sec. 3) taken at the off-surface
  * target: modal Green's functions of the source rings seen from x, the
  * outer integral graded toward the nearest surface point (found on the host
- * by Levenberg-Marquardt from the nearest node, qams_nearest_surface_point).  The result is then the layer
- * potential of the interpolated density on those panels, accurate at any
- * distance off the surface; points on a surface are not supported.  mu_dev
+ * by Levenberg-Marquardt from the nearest node, qams_nearest_surface_point).
+ * The result is then the layer potential of the interpolated density on
+ * those panels, accurate at any distance off the surface; points on a
+ * surface are not supported.  mu_dev
  * [N][R] and u_dev [M][R] are complex128.  Blocking on `stream`.
  * Errors: QAMS_EINVAL (also a near point whose ring bandwidth k (r + d)
  * exceeds the self-block kernel's tables, as qams_assemble), QAMS_EBUDGET,
